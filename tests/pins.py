@@ -1,0 +1,334 @@
+"""Pins of the CPU oracle against facts it does not itself compute.
+
+Each function returns a scalar discrepancy (0 when the oracle is right) so that
+``test_oracle_*`` assert it is small and ``test_oracle_mutations`` can check
+that a planted mistake in the oracle makes at least one of them large.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+
+import numpy as np
+import scipy.linalg
+import scipy.sparse.linalg
+
+import workloads as W
+from oracle import arnoldi as OA
+from oracle import exact as OE
+from oracle import expm as OX
+from oracle import krylov as OK
+from oracle import operators as OP
+from oracle import phi as OPHI
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def unit_vectors(N, j, coupling, seed):
+    """j random unit vectors with mutual inner products of order ``coupling``."""
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((N, j)))
+    V = Q + coupling * rng.standard_normal((N, j)) / math.sqrt(N)
+    return V / np.linalg.norm(V, axis=0)
+
+
+def drive_correction(cls, V, b=None):
+    """Feed the hybrid correction class the inner products of the columns of V
+    step by step (temp column 1 = V_{1:j-1}^T v_j), as Alg. 4 would; at the
+    last step column 2 is b.  Returns (object, result of the last form())."""
+    j = V.shape[1]
+    obj = cls(j)
+    out = None
+    for jj in range(2, j + 1):
+        temp = np.zeros((jj + 1, 2))
+        temp[:jj - 1, 0] = V[:, :jj - 1].T @ V[:, jj - 1]
+        temp[:jj, 1] = b[:jj] if (b is not None and jj == j) else 0.0
+        out = obj.form(temp, jj)
+    return obj, out
+
+
+# --- phi -------------------------------------------------------------------
+
+def pin_phi_at_zero():
+    return max(abs(OPHI.phi(k, 0.0) - 1.0 / math.factorial(k)) for k in range(8))
+
+
+def pin_phi_quadrature():
+    err = 0.0
+    for z in [1e-6, -0.3, 0.9, 1.9, 2.1, -7.5, 3.0 + 4.0j, -0.5 + 0.1j, -12.0 - 6.0j]:
+        for k in range(5):
+            ref = OPHI.phi_quadrature(k, z)
+            val = complex(OPHI.phi(k, np.array([z], dtype=complex))[0])
+            err = max(err, abs(val - ref) / max(1e-300, abs(ref)))
+    return err
+
+
+# --- small exponential -----------------------------------------------------
+
+def pin_expm_vs_scipy():
+    rng = np.random.default_rng(7)
+    err = 0.0
+    for n, scale in [(5, 0.1), (12, 3.0), (33, 8.0), (41, 20.0)]:
+        A = rng.standard_normal((n, n)) * scale / math.sqrt(n)
+        E = OX.expm_taylor(A)
+        R = scipy.linalg.expm(A)
+        err = max(err, np.linalg.norm(E - R) / np.linalg.norm(R))
+    return err
+
+
+def pin_expm_nilpotent_shift():
+    n = 7
+    S = np.diag(np.ones(n - 1), 1)
+    ref = sum(np.linalg.matrix_power(S, k) / math.factorial(k) for k in range(n))
+    return np.abs(OX.expm_taylor(S) - ref).max()
+
+
+def pin_expm_diagonal():
+    lam = np.array([-30.0, -1.0, 0.0, 0.5, 4.0])
+    return np.abs(OX.expm_taylor(np.diag(lam)) - np.diag(np.exp(lam))).max() / math.exp(4.0)
+
+
+# --- operators ---------------------------------------------------------------
+
+def pin_advdiff_fourier(cfg=None):
+    cfg = cfg or W.advdiff2d(8, ny=6, vel=(1.0, -0.5))
+    nx, ny = cfg["nx"], cfg["ny"]
+    A = OP.advdiff2d(nx, ny, cfg["dx"], cfg["diff"], cfg["vel"])
+    lam = OP.fourier_symbol_advdiff2d(nx, ny, cfg["dx"], cfg["diff"], cfg["vel"])
+    ix, iy = np.meshgrid(np.arange(nx), np.arange(ny))
+    err = 0.0
+    for kx in range(nx):
+        for ky in range(ny):
+            mode = np.exp(2j * np.pi * (kx * ix / nx + ky * iy / ny)).reshape(-1)
+            err = max(err, np.abs(A @ mode - lam[ky, kx] * mode).max() / (1 + abs(lam[ky, kx])))
+    return err
+
+
+def pin_adr_fourier():
+    nx, ny, nz, dx = 5, 4, 3, 0.2
+    vel = (1.0, 0.5, -2.0)
+    A = OP.adr3d(nx, ny, nz, dx, 0.03, vel, np.full(nx * ny * nz, -0.25))
+    lam = OP.fourier_symbol_adr3d(nx, ny, nz, dx, 0.03, vel, -0.25)
+    iz, iy, ix = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    err = 0.0
+    for kx in range(nx):
+        for ky in range(ny):
+            for kz in range(nz):
+                mode = np.exp(2j * np.pi * (kx * ix / nx + ky * iy / ny + kz * iz / nz)).reshape(-1)
+                err = max(err, np.abs(A @ mode - lam[kz, ky, kx] * mode).max())
+    return err
+
+
+def grayscott_rhs(u, v, nx, ny, dx, Du, Dv, F, k):
+    """The Gray-Scott PDE right-hand side with a periodic 5-point Laplacian,
+    written with np.roll on (ny, nx) fields."""
+    def lap(f):
+        f = f.reshape(ny, nx)
+        return ((np.roll(f, 1, 0) + np.roll(f, -1, 0) + np.roll(f, 1, 1) + np.roll(f, -1, 1)
+                 - 4 * f) / dx**2).reshape(-1)
+    return (Du * lap(u) - u * v * v + F * (1 - u), Dv * lap(v) + u * v * v - (F + k) * v)
+
+
+def pin_grayscott_jacobian():
+    nx, ny, dx = 7, 5, 0.3
+    Du, Dv, F, k = 2e-2, 1e-2, 0.04, 0.06
+    rng = np.random.default_rng(3)
+    u0, v0 = rng.uniform(0, 1, nx * ny), rng.uniform(0, 1, nx * ny)
+    J = OP.grayscott2d(nx, ny, dx, Du, Dv, F, k, u0, v0)
+    d = rng.uniform(-1, 1, 2 * nx * ny)
+    eps = 1e-6
+    n = nx * ny
+    fp = np.concatenate(grayscott_rhs(u0 + eps * d[:n], v0 + eps * d[n:], nx, ny, dx, Du, Dv, F, k))
+    fm = np.concatenate(grayscott_rhs(u0 - eps * d[:n], v0 - eps * d[n:], nx, ny, dx, Du, Dv, F, k))
+    fd = (fp - fm) / (2 * eps)
+    return np.abs(J @ d - fd).max() / np.abs(fd).max()
+
+
+# --- correction matrices ------------------------------------------------------
+
+def pin_t3_worked_example():
+    with open(os.path.join(GOLDEN, "t3_worked_example.json")) as f:
+        g = json.load(f)
+    V = unit_vectors(40, 3, 0.3, 11)
+    a = V.T @ V
+    env = dict(a21=a[1, 0], a31=a[2, 0], a32=a[2, 1])
+    err = 0.0
+    for key, cls in [("cwy", OA.CWY), ("ncwy", OA.NCWY)]:
+        ref = np.array([[eval(e, {}, env) for e in row] for row in g[key]], dtype=float)
+        obj, _ = drive_correction(cls, V)
+        err = max(err, np.abs(obj.T[:3, :3] - ref).max())
+    return err
+
+
+def pin_cwy_projector_identity():
+    """Eq. 20: (I - v_j v_j^T) ... (I - v_1 v_1^T) = I - V_j T_j V_j^T with T_j
+    from the recursion Eq. 21, for non-orthogonal unit vectors."""
+    err = 0.0
+    for j in (2, 5, 9):
+        V = unit_vectors(30, j, 0.4, 20 + j)
+        P = np.eye(30)
+        for i in range(j):
+            P = (np.eye(30) - np.outer(V[:, i], V[:, i])) @ P
+        obj, _ = drive_correction(OA.CWY, V)
+        err = max(err, np.abs(P - (np.eye(30) - V @ obj.T[:j, :j] @ V.T)).max())
+    return err
+
+
+def pin_gsmgs_two_sweeps():
+    """Sect. 3.2.3: T_j b equals two Gauss-Seidel sweeps on V^T V x = b from
+    x^0 = 0 (sweeps written element by element here)."""
+    err = 0.0
+    for j in (2, 4, 8):
+        V = unit_vectors(50, j, 0.3, 40 + j)
+        G = V.T @ V
+        b = np.random.default_rng(j).standard_normal(j)
+        x = np.zeros(j)
+        for _ in range(2):
+            xn = np.zeros(j)
+            for i in range(j):
+                s = b[i] - sum(G[i, l] * xn[l] for l in range(i)) \
+                         - sum(G[i, l] * x[l] for l in range(i + 1, j))
+                xn[i] = s / G[i, i]
+            x = xn
+        _, out = drive_correction(OA.GSMGS, V, b)
+        err = max(err, np.abs(out - x).max())
+    return err
+
+
+def pin_norm_estimate_orthonormal():
+    """Eq. 18 is exact for an orthonormal basis (Pythagoras)."""
+    rng = np.random.default_rng(5)
+    Q, _ = np.linalg.qr(rng.standard_normal((60, 9)))
+    w = rng.standard_normal(60)
+    est = math.sqrt(w @ w - np.sum((Q.T @ w) ** 2))
+    return abs(est - np.linalg.norm(w - Q @ (Q.T @ w)))
+
+
+# --- Arnoldi ----------------------------------------------------------------------
+
+def small_problem(seed=0):
+    cfg = W.advdiff2d(12, ny=10, diff=0.01, vel=(1.0, 0.5))
+    cfg["seed"] = W.SEED_BASE + 100 + seed
+    inp = W.make_inputs(cfg)
+    A = OP.from_workload(cfg, inp)
+    return cfg, inp, A
+
+
+def pin_mgs_vs_qr():
+    """The Arnoldi basis with positive subdiagonal is the Q factor (positive
+    diagonal R) of the Krylov matrix [b, Ab, ..., A^{m-1} b]."""
+    cfg, inp, A = small_problem()
+    A = A / 50.0
+    b = inp["v"]
+    m = 6
+    K = np.zeros((b.size, m))
+    K[:, 0] = b
+    for i in range(1, m):
+        K[:, i] = A @ K[:, i - 1]
+    Q, R = np.linalg.qr(K)
+    Q = Q * np.sign(np.diag(R))
+    res = OA.mgs(lambda x: A @ x, b, m)
+    return np.abs(res["V"][:, :m] - Q).max()
+
+
+def pin_variants_equal_mgs(variants=("cgs2", "hcwy", "hncwy", "hgsmgs")):
+    cfg, inp, A = small_problem()
+    ref = OA.mgs(lambda x: A @ x, inp["v"], 25)
+    err = 0.0
+    for var in variants:
+        res = OA.arnoldi(lambda x: A @ x, inp["v"], 25, var)
+        err = max(err, np.abs(res["H"] - ref["H"]).max() / np.abs(ref["H"]).max(),
+                  np.abs(res["V"] - ref["V"]).max(), abs(res["beta"] - ref["beta"]) / ref["beta"])
+    return err
+
+
+def pin_arnoldi_relation(variant):
+    cfg, inp, A = small_problem()
+    res = OA.arnoldi(lambda x: A @ x, inp["v"], 25, variant)
+    V, H = res["V"], res["H"]
+    m = H.shape[1]
+    R = A @ V[:, :m] - V @ H
+    return np.linalg.norm(R) / (scipy.sparse.linalg.norm(A) * np.linalg.norm(V))
+
+
+# --- phi products -------------------------------------------------------------------
+
+def pin_krylov_vs_dense(variant="mgs"):
+    cfg = W.advdiff2d(6, ny=5, diff=0.02, vel=(1.0, -0.7))
+    inp = W.make_inputs(cfg)
+    A = OP.from_workload(cfg, inp)
+    ref = OE.phi_products_dense(A, inp["v"], 0.05, 3, expm=scipy.linalg.expm)
+    y, _ = OK.phiv(lambda x: A @ x, inp["v"], 0.05, 3, 24, variant)
+    return max(np.linalg.norm(y[k] - ref[k]) / np.linalg.norm(ref[k]) for k in range(4))
+
+
+def pin_krylov_grayscott_vs_dense(variant="hcwy"):
+    cfg = W.grayscott2d(12, Du=2e-3, Dv=1e-3)
+    inp = W.make_inputs(cfg)
+    A = OP.from_workload(cfg, inp)
+    ref = OE.phi_products_dense(A, inp["v"], 1.0, 2, expm=scipy.linalg.expm)
+    y, _ = OK.phiv(lambda x: A @ x, inp["v"], 1.0, 2, 40, variant)
+    return max(np.linalg.norm(y[k] - ref[k]) / np.linalg.norm(ref[k]) for k in range(3))
+
+
+def pin_krylov_vs_fft_config1(variant="mgs"):
+    cfg = W.config(0)
+    inp = W.make_inputs(cfg)
+    A = OP.from_workload(cfg, inp)
+    ref = OE.phi_products_fft_advdiff2d(cfg, inp["v"], cfg["h"], cfg["p"])
+    y, _ = OK.phiv(lambda x: A @ x, inp["v"], cfg["h"], cfg["p"], cfg["m"], variant)
+    return max(np.linalg.norm(y[k] - ref[k]) / np.linalg.norm(ref[k]) for k in range(cfg["p"] + 1))
+
+
+def pin_krylov_vs_fft_adr(variant="hgsmgs"):
+    cfg = W.adr3d(16, m=40)
+    inp = W.make_inputs(cfg)
+    r = np.full(16**3, -0.5)
+    A = OP.adr3d(16, 16, 16, cfg["dx"], cfg["diff"], cfg["vel"], r)
+    h = 0.02
+    ref = OE.phi_products_fft_adr3d(cfg, inp["v"], h, 1, -0.5)
+    y, _ = OK.phiv(lambda x: A @ x, inp["v"], h, 1, 40, variant)
+    return max(np.linalg.norm(y[k] - ref[k]) / np.linalg.norm(ref[k]) for k in range(2))
+
+
+def pin_diagonal_breakdown(variant):
+    """Diagonal A with 3 distinct eigenvalues: the Krylov space is 3-dimensional,
+    Arnoldi breaks down at step 3 and the product is exact."""
+    rng = np.random.default_rng(9)
+    lam = rng.choice([-3.0, -0.5, 1.2], size=200)
+    v = rng.uniform(-1, 1, 200)
+    y, info = OK.phiv(lambda x: lam * x, v, 0.7, 2, 10, variant)
+    ref = OE.phi_products_diagonal(lam, v, 0.7, 2)
+    err = max(np.linalg.norm(y[k] - ref[k]) / np.linalg.norm(ref[k]) for k in range(3))
+    return err + abs(info["m_eff"] - 3)
+
+
+def pin_zero_operator(variant):
+    v = np.random.default_rng(2).uniform(-1, 1, 50)
+    y, info = OK.phiv(lambda x: 0.0 * x, v, 0.3, 3, 8, variant)
+    err = max(np.abs(y[k] - v / math.factorial(k)).max() for k in range(4))
+    return err + abs(info["m_eff"] - 1)
+
+
+def pin_h_zero(variant):
+    cfg, inp, A = small_problem()
+    y, _ = OK.phiv(lambda x: A @ x, inp["v"], 0.0, 3, 10, variant)
+    return max(np.abs(y[k] - inp["v"] / math.factorial(k)).max() for k in range(4))
+
+
+def pin_sync_counts():
+    """Sect. 2.3 and Alg. 4 sync counts (tests/golden/sync_counts.json)."""
+    cfg, inp, A = small_problem()
+    mv = lambda x: A @ x
+    m = 12
+    bad = 0
+    r = OA.mgs(mv, inp["v"], m)
+    bad += sum(s != j + 1 for j, s in enumerate(r["syncs"], start=1))
+    r = OA.cgs2(mv, inp["v"], m)
+    bad += sum(s != 3 for s in r["syncs"])
+    for var in ("hcwy", "hncwy", "hgsmgs"):
+        r = OA.arnoldi(mv, inp["v"], m, var)
+        expect = [1 + (1 if j == m else 0) for j in range(1, m + 1)]
+        bad += sum((s - f) != e for s, e, f in zip(r["syncs"], expect, [0] * m)) if r["fallbacks"] == 0 else 0
+    return float(bad)

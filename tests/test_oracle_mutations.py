@@ -1,0 +1,87 @@
+"""Planted mistakes in the oracle (on the CPU) must trip at least one pin.
+
+Each case monkeypatches one plausible slip -- a dropped term, a wrong sign, a
+wrong index, a transposed operand -- and checks that the pins which should
+guard that spot report a large discrepancy."""
+import numpy as np
+
+from oracle import arnoldi as OA
+from oracle import krylov as OK
+from oracle import operators as OP
+from tests import pins
+
+
+def test_cwy_sign_slip_is_caught(monkeypatch):
+    def bad_form(self, temp, j):
+        T = self.T
+        T[j - 1, :j - 1] = +(temp[:j - 1, 0] @ T[:j - 1, :j - 1])   # sign flipped
+        return T[:j, :j] @ temp[:j, 1]
+    monkeypatch.setattr(OA.CWY, "form", bad_form)
+    assert pins.pin_cwy_projector_identity() > 1e-3
+    assert pins.pin_t3_worked_example() > 1e-3
+
+
+def test_cwy_dropped_product_is_caught(monkeypatch):
+    # dropping the T_{j-1} factor turns CWY into NCWY: the T_3 example catches it
+    monkeypatch.setattr(OA.CWY, "form", OA.NCWY.form)
+    assert pins.pin_t3_worked_example() > 1e-4
+    assert pins.pin_cwy_projector_identity() > 1e-4
+
+
+def test_gsmgs_transposed_splitting_is_caught(monkeypatch):
+    def bad_form(self, temp, j):
+        M, Minv, N = self.M, self.Minv, self.N
+        M[j - 1, :j - 1] = temp[:j - 1, 0]
+        N[:j - 1, j - 1] = -temp[:j - 1, 0]
+        Minv[j - 1, :j - 1] = -(temp[:j - 1, 0] @ Minv[:j - 1, :j - 1])
+        pvec = temp[:j, 1] + N[:j, :j].T @ (Minv[:j, :j] @ temp[:j, 1])   # N transposed
+        return np.linalg.solve(M[:j, :j], pvec)
+    monkeypatch.setattr(OA.GSMGS, "form", bad_form)
+    assert pins.pin_gsmgs_two_sweeps() > 1e-3
+
+
+def test_hybrid_missing_second_scaling_is_caught(monkeypatch):
+    orig = OA.hybrid
+
+    def bad_hybrid(matvec, b, m, variant="hcwy"):
+        # scale A by the first true norm: models forgetting one 1/true_nrm on temp
+        state = {}
+        def mv(x):
+            return matvec(x) * state.setdefault("s", 1.0 + 1e-3)
+        return orig(mv, b, m, variant)
+    monkeypatch.setattr(OA, "hybrid", bad_hybrid)
+    monkeypatch.setitem(OA.VARIANTS, "hcwy", lambda f, b, m: bad_hybrid(f, b, m, "hcwy"))
+    assert pins.pin_variants_equal_mgs(("hcwy",)) > 1e-4
+
+
+def test_augmentation_index_slip_is_caught(monkeypatch):
+    def bad_aug(H, h, p):
+        m = H.shape[1]
+        n = m + p + 1
+        Hh = np.zeros((n, n))
+        Hh[:m, :m] = h * H[:m, :m]
+        Hh[m - 1, m] = 1.0                     # e_m instead of e_1
+        for i in range(p):
+            Hh[m + i, m + i + 1] = 1.0
+        return Hh
+    monkeypatch.setattr(OK, "augmented_hessenberg", bad_aug)
+    assert pins.pin_krylov_vs_dense("mgs") > 1e-3
+    assert pins.pin_krylov_vs_fft_config1("mgs") > 1e-3
+
+
+def test_advection_sign_slip_is_caught(monkeypatch):
+    orig = OP.central_difference
+    monkeypatch.setattr(OP, "central_difference", lambda n, dx: -orig(n, dx))
+    assert pins.pin_advdiff_fourier() > 1e-3
+
+
+def test_grayscott_coupling_slip_is_caught(monkeypatch):
+    import scipy.sparse as sp
+    def bad(nx, ny, dx, Du, Dv, F, k, u0, v0):
+        n = nx * ny
+        lap = OP._axis_ops((nx, ny), [OP.second_difference(nx, dx), OP.second_difference(ny, dx)])
+        I = sp.identity(n, format="csr")
+        a, b = sp.diags(v0 * v0), sp.diags(2.0 * u0 * v0)
+        return sp.bmat([[Du * lap - a - F * I, b], [a, Dv * lap + b - (F + k) * I]], format="csr")
+    monkeypatch.setattr(OP, "grayscott2d", bad)
+    assert pins.pin_grayscott_jacobian() > 1e-3
