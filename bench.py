@@ -1,0 +1,359 @@
+"""Benchmark of the phi-product hot path on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--config I] [--variant hcwy] [--precision fp64]
+
+A step is one phiv call -- the whole hot path (stencil matvecs, grouped
+reductions, correction, projection, small exponential, output combination) over
+one synthetic input.  Default workload: the Gray-Scott Jacobian on a 512x512
+periodic grid (N = 524288), phi_0..phi_2 with m = 64, float64, hybrid
+one-reduce Arnoldi with the compact-WY correction.
+
+Prints one JSON line (rank 0).  Under torchrun every rank runs an independent
+replica (the path is not sharded: one phi product fits one GPU), the time is
+the max over ranks and value = all ranks' phiv calls / that time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Arnoldi steps/s and phiv calls/s at 1e-10 rel err; HBM GB/s fraction; grid syncs/step"
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+# FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (recipe's unit counts and clock)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", type=int, default=1)
+    ap.add_argument("--variant", default="hcwy")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--no-flush", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle leg (profiling runs)")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_PATH) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def workload(cfg_index):
+    import workloads as W
+
+    cfg = W.config(cfg_index)
+    if cfg.get("kind") == "batched":
+        raise SystemExit("the batched workload is a parity case, not a bench line")
+    return cfg
+
+
+def algorithmic_counts(cfg, precision, m_eff):
+    """Algorithmic bytes and FP64 flops of one Arnoldi launch (hybrid form).
+
+    Step j (1-based) reads the j-1 previous columns and w_{j-1}, writes x_j and
+    w_j (the stencil is fused, halos excluded): (j+2) N elements; the operator's
+    coefficient fields add their own reads.  The final projection reads m
+    columns and w_m and writes v_{m+1}: (m+2) N.  Flops: projection 2(j-1) N,
+    dots 2(2(j-1)+3) N, stencil ~2*taps N per step; final 2m N."""
+    import workloads as W
+
+    N = W.n_dof(cfg)
+    bs = 8 if precision == "fp64" else 4
+    fb = 8 if precision == "fp64" else 4
+    field_elems = {"advdiff2d": 0, "grayscott2d": N, "adr3d": N}[cfg["kind"]]
+    taps = {"advdiff2d": 5, "grayscott2d": 7, "adr3d": 8}[cfg["kind"]]
+    m = m_eff
+    elems = sum(j + 2 for j in range(1, m + 1)) * N + (m + 2) * N
+    byts = elems * bs + m * field_elems * fb
+    flops = sum(2 * (j - 1) + 2 * (2 * (j - 1) + 3) + 2 * taps for j in range(1, m + 1)) * N
+    flops += (2 * m + 2) * N
+    return byts, flops
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, val in zip(names, r[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def run_reference(args, world, rank):
+    """The CPU oracle (float64 NumPy) timed on this host on a bounded sample."""
+    if rank != 0:
+        return
+    import numpy as np
+
+    import workloads as W
+    from oracle import krylov as OK
+    from oracle import operators as OP
+
+    cfg = workload(args.config)
+    inp = W.make_inputs(cfg)
+    A = OP.from_workload(cfg, inp)
+    variant = args.variant
+    for _ in range(min(args.warmup, 1)):
+        OK.phiv(lambda x: A @ x, inp["v"], cfg["h"], cfg["p"], cfg["m"], variant)
+    t_steps = []
+    t0 = time.perf_counter()
+    n = 0
+    while n < max(1, args.steps):
+        ts = time.perf_counter()
+        OK.phiv(lambda x: A @ x, inp["v"], cfg["h"], cfg["p"], cfg["m"], variant)
+        t_steps.append(time.perf_counter() - ts)
+        n += 1
+        if time.perf_counter() - t0 > 9 * args.cpu_budget:   # keep the run within minutes
+            break
+    tot = sum(t_steps)
+    value = n / tot
+    cores = os.cpu_count()
+    sample = f"{n} full phiv call(s) of {cfg['name']} (m={cfg['m']}, p={cfg['p']}, {variant})"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "phiv/s",
+            "n_gpus": world, "steps": n, "warmup": 0, "ms_per_step": 1e3 * tot / n,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": cfg["name"], "m": cfg["m"], "p": cfg["p"],
+                                             "variant": variant, "precision": "fp64"},
+            "cpu_baseline": {"value": value, "unit": "phiv/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "phiv/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(cfg, variant, budget):
+    """Time the oracle (as it stands) on a bounded sample: whole phiv calls on
+    the full workload until ~budget seconds have passed.  Also returns the last
+    oracle result for the accuracy check of the GPU result."""
+    import workloads as W
+    from oracle import krylov as OK
+    from oracle import operators as OP
+
+    inp = W.make_inputs(cfg)
+    A = OP.from_workload(cfg, inp)
+    t0 = time.perf_counter()
+    n = 0
+    y = None
+    while True:
+        y, _ = OK.phiv(lambda x: A @ x, inp["v"], cfg["h"], cfg["p"], cfg["m"], variant)
+        n += 1
+        if time.perf_counter() - t0 > budget or n >= 5:
+            break
+    el = time.perf_counter() - t0
+    return {"value": n / el, "unit": "phiv/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{n} full phiv call(s) of {cfg['name']} ({variant}, float64 NumPy/SciPy)"}, y
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import numpy as np
+    import torch
+
+    import paper_2410_14917_gb300 as lsa
+    import workloads as W
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfg = workload(args.config)
+    inp = W.make_inputs(cfg)
+    N = W.n_dof(cfg)
+    p, m, h = cfg["p"], cfg["m"], cfg["h"]
+    fields = {k: torch.from_numpy(v).to(dev) for k, v in inp.items() if k != "v"}
+    v_host = torch.from_numpy(inp["v"]).pin_memory()
+    v = v_host.to(dev)
+    op = lsa.Operator.from_workload(cfg, fields)
+    work = lsa.Workspace.for_call(op, m, p, args.precision)
+    y = torch.empty((p + 1, N), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    flush = None if args.no_flush else torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    # first call: status and statistics
+    _, st0 = lsa.phiv(op, v, h, p, m, variant=args.variant, precision=args.precision, y=y, work=work)
+    m_eff = st0["m_eff"]
+    for _ in range(args.warmup):
+        lsa.phiv(op, v, h, p, m, variant=args.variant, precision=args.precision, y=y, work=work,
+                 stats=False)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    k_arn = []
+    k_exp = []
+    k_cmb = []
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        if flush is not None:
+            flush.fill_(i & 0xFF)           # evict L2 between timed steps
+        ev[i][0].record(stream)
+        _, st = lsa.phiv(op, v, h, p, m, variant=args.variant, precision=args.precision, y=y,
+                         work=work, stats=True)
+        ev[i][1].record(stream)
+        if st["status"] < 0:
+            raise RuntimeError(f"phiv failed: {st}")
+        k_arn.append(st["ms_arnoldi"])
+        k_exp.append(st["ms_expm"])
+        k_cmb.append(st["ms_combine"])
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    tot_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([tot_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    value = world * args.steps / (tot_ms / 1e3)
+
+    # end-to-end through the public API with host buffers: H2D of v, phiv, D2H of y
+    y_host = torch.empty((p + 1, N), dtype=torch.float64).pin_memory()
+    e2e_steps = max(3, min(args.steps, 10))
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(e2e_steps):
+        v_dev = v_host.to(dev, non_blocking=True)
+        lsa.phiv(op, v_dev, h, p, m, variant=args.variant, precision=args.precision, y=y, work=work,
+                 stats=False)
+        y_host.copy_(y, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_value = e2e_steps / (e0.elapsed_time(e1) / 1e3) * world
+
+    # roofline of the dominant kernel (the persistent Arnoldi kernel)
+    byts, flops = algorithmic_counts(cfg, args.precision, m_eff)
+    ms_a = statistics.mean(k_arn)
+    hbm_peak, peak_kind = load_peaks()
+    if args.precision == "fp64":
+        achieved = flops / (ms_a / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "kernel": "k_arnoldi (persistent hybrid Arnoldi)",
+                "peak_source": "FP64 FMA pipe from unit counts and max clock (152 SMs x 2 FMA/clk x 2.07 GHz)",
+                "hbm_gbs": byts / (ms_a / 1e3) / 1e9, "hbm_frac": byts / (ms_a / 1e3) / 1e9 / hbm_peak,
+                "algorithmic_bytes": byts, "algorithmic_flops": flops}
+    else:
+        achieved = byts / (ms_a / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None,
+                "kernel": "k_arnoldi (persistent hybrid Arnoldi)", "peak_source": f"{peak_kind} hbm_gbs",
+                "algorithmic_bytes": byts, "algorithmic_flops": flops}
+
+    line = {"metric": METRIC, "value": value, "unit": "phiv/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32-basis/f64",
+            "data": "synthetic",
+            "config": {"workload": cfg["name"], "N": N, "m": m, "p": p, "h": h,
+                       "variant": args.variant, "precision": args.precision,
+                       "l2": "flushed between timed steps (256 MiB write)" if flush is not None
+                       else "not flushed; basis working set > L2",
+                       "parallelism": f"replicas x{world}"},
+            "arnoldi_steps_per_s": value * m_eff,
+            "grid_syncs_per_step": st0["grid_syncs"] / max(m_eff, 1),
+            "kernel_ms": {"arnoldi": ms_a, "expm": statistics.mean(k_exp),
+                          "combine": statistics.mean(k_cmb)},
+            "roofline": roof,
+            "e2e": {"value": e2e_value, "unit": "phiv/s", "h2d_bytes_per_step": N * 8,
+                    "d2h_bytes_per_step": (p + 1) * N * 8},
+            "gpu_launches": 4 * args.steps,
+            "clocks": clocks}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cb, y_ref = cpu_baseline(cfg, "mgs", args.cpu_budget)
+        line["cpu_baseline"] = cb
+        yc = y.cpu().numpy()
+        line["rel_err_vs_oracle"] = max(float(np.linalg.norm(yc[k] - y_ref[k]) / np.linalg.norm(y_ref[k]))
+                                        for k in range(p + 1))
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,168 @@
+/*
+ * lsarnoldi -- Krylov phi-function products with low-synchronisation Arnoldi
+ * on one GB300 (sm_103a).  C ABI: plain pointers and sizes only.
+ *
+ * The library computes, for a matrix-free stencil operator A,
+ *     y_k = phi_k(h A) v,   k = 0..p,
+ * by an m-step Arnoldi projection (Sect. 2.2, Eq. 13: e^A b ~ ||b|| V_m e^{H_m} e_1)
+ * with the phi-functions of Sect. 2 (Eqs. 5-6) read off one exponential of the
+ * small augmented Hessenberg matrix (the m-sized analogue of Sect. 2.1, Eqs. 7-9).
+ * The Gram-Schmidt step is one of
+ *   LSA_MGS     Alg. 1 (modified Gram-Schmidt, j+1 reductions at step j),
+ *   LSA_CGS2    classical Gram-Schmidt applied twice (textbook; 3 reductions
+ *               per step; Sect. 2.3 discusses classical GS),
+ *   LSA_HCWY    Alg. 4 with the compact-WY correction of Alg. 5 (Sect. 3.2.1),
+ *   LSA_HNCWY   Alg. 4 with the truncated Neumann correction of Alg. 6 (Sect. 3.2.2),
+ *   LSA_HGSMGS  Alg. 4 with the two-sweep Gauss-Seidel correction of Alg. 7 (Sect. 3.2.3);
+ * the three hybrid variants need one global reduction per Arnoldi step.
+ *
+ * Conventions for every entry point:
+ *  - Device pointers ("dev") point to memory on the current CUDA device; the
+ *    caller owns and allocates every buffer, including the workspace.  The
+ *    library never allocates device memory.
+ *  - Vectors are contiguous.  Grid index i = ix + nx*(iy + ny*iz), x fastest;
+ *    Gray-Scott stacks the species as [u-block; v-block] (N = 2*nx*ny).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Work is enqueued asynchronously.  When `stats` is non-NULL the call
+ *    synchronises the stream, fills *stats and returns the device-side status
+ *    (which may be LSA_BREAKDOWN, LSA_NOT_CONVERGED or LSA_ERR_TIMEOUT);
+ *    with stats == NULL only argument and launch errors are reported, and
+ *    lsa_read_stats() retrieves the rest later.
+ *  - No exception or longjmp crosses the ABI; errors are status codes.
+ *  - Statuses >= 0 leave valid outputs; statuses < 0 leave outputs undefined.
+ */
+#ifndef LSARNOLDI_H
+#define LSARNOLDI_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LSA_OK = 0,
+  LSA_BREAKDOWN = 1,        /* lucky breakdown at step m_eff < m; result exact in the subspace */
+  LSA_NOT_CONVERGED = 2,    /* a-posteriori estimate err_est > tol * beta */
+  LSA_ERR_ARG = -1,         /* invalid argument (null pointer, size, enum, m out of range...) */
+  LSA_ERR_CUDA = -2,        /* a CUDA runtime call failed */
+  LSA_ERR_TIMEOUT = -3,     /* an in-kernel grid barrier gave up waiting (bounded spin) */
+  LSA_ERR_NUMERIC = -4,     /* non-finite value in H or in a norm */
+  LSA_ERR_WORKSPACE = -5    /* workspace too small or misaligned (needs 256-byte alignment) */
+} lsa_status;
+
+typedef enum { LSA_MGS = 0, LSA_CGS2 = 1, LSA_HCWY = 2, LSA_HNCWY = 3, LSA_HGSMGS = 4 } lsa_variant;
+
+/* LSA_FP64: basis, matvec and all reductions in IEEE double.
+ * LSA_FP32_BASIS: basis vectors and the stencil matvec in float; inner products
+ * with float products, short float runs and compensated (Kahan) accumulation,
+ * reduced across the GPU in double; H, the correction matrices, the norm
+ * estimate and the small exponential stay in double. */
+typedef enum { LSA_FP64 = 0, LSA_FP32_BASIS = 1 } lsa_precision;
+
+typedef enum { LSA_OP_ADVDIFF2D = 1, LSA_OP_GRAYSCOTT2D = 2, LSA_OP_ADR3D = 3 } lsa_op_kind;
+
+/* Operator descriptor (plain data; the library only borrows the field pointers).
+ *  LSA_OP_ADVDIFF2D  periodic nx*ny grid:  A v = diff*Lap5 v - vel[0]*Dx v - vel[1]*Dy v,
+ *                    central differences; nz must be 1.
+ *  LSA_OP_GRAYSCOTT2D Jacobian of Gray-Scott at (u0, v0) = (field0, field1), each nx*ny:
+ *                    [[diff*Lap - v0^2 - F, -2 u0 v0], [v0^2, diff2*Lap + 2 u0 v0 - (F+k)]];
+ *                    nz must be 1, N = 2*nx*ny.
+ *  LSA_OP_ADR3D      periodic nx*ny*nz grid: A v = diff*Lap7 v - sum_a vel[a]*Upwind_a v + r.*v,
+ *                    r = field0 (N values), first-order upwind differences.
+ * All operators use the uniform spacing dx in every direction. */
+typedef struct {
+  int kind;
+  int nx, ny, nz;
+  double dx;
+  double diff;
+  double diff2;
+  double vel[3];
+  double F, k;
+  const double* field0;   /* dev, see above; NULL when unused */
+  const double* field1;   /* dev, see above; NULL when unused */
+} lsa_op;
+
+typedef struct {
+  int status;             /* device-side lsa_status of the last call on this workspace */
+  int m_eff;              /* completed Arnoldi steps */
+  int breakdown;          /* 1 after a lucky breakdown */
+  int norm_fallbacks;     /* explicit-norm fallbacks of the hybrid norm estimate (Alg. 4) */
+  int grid_syncs;         /* global reductions performed (in-kernel grid barriers with reduction) */
+  int grid_barriers;      /* all grid barriers, including those without a reduction */
+  double beta;            /* ||v|| */
+  double err_est;         /* beta*h*H_{m+1,m}*|e_m^T phi_{p+1}(h H_m) e_1| (phiv only) */
+  double h_last;          /* H_{m+1,m} */
+  float ms_arnoldi;       /* device time of the Arnoldi kernel (CUDA events; filled when stats != NULL) */
+  float ms_expm;          /* device time of the small exponential (phiv only) */
+  float ms_combine;       /* device time of the output combination (phiv only) */
+  int launches;           /* kernels this call launched */
+} lsa_stats;
+
+/* Largest supported Krylov dimension m. */
+int lsa_max_m(void);
+
+/* Library version (major*10000 + minor*100 + patch). */
+int lsa_version(void);
+
+/* Human-readable name of a status code (static string). */
+const char* lsa_status_string(int status);
+
+/* Number of unknowns N of an operator (-1 if the descriptor is invalid). */
+long long lsa_op_dof(const lsa_op* op);
+
+/* Bytes of device workspace needed by lsa_phiv / lsa_arnoldi for (op, m, p,
+ * precision) on the current device; 0 if the arguments are invalid.  The
+ * workspace must be 256-byte aligned.  Its contents need not be initialised. */
+size_t lsa_workspace_bytes(const lsa_op* op, int m, int p, int precision);
+
+/* S1 alone: y = A x.  x, y: dev, N elements of the basis type (double for
+ * LSA_FP64, float for LSA_FP32_BASIS).  Uses the same stencil code as the
+ * Arnoldi kernels.  work: dev workspace of lsa_workspace_bytes(op, 1, 0, precision). */
+lsa_status lsa_matvec(const lsa_op* op, const void* x, void* y, int precision,
+                      void* work, size_t work_bytes, void* stream);
+
+/* Arnoldi decomposition A V_m = V_{m+1} Hbar_m (Sect. 2.2, Eq. 12).
+ *  v  dev, N doubles: start vector b (not modified).
+ *  m  1 <= m <= min(lsa_max_m(), N).
+ *  V  dev, N x (m+1) column-major (leading dimension N) of the basis type; on
+ *     return columns 0..m_eff hold the orthonormal basis (column m_eff is
+ *     v_{m_eff+1}; after a breakdown it is unspecified).
+ *  H  dev, (m+1) x m column-major doubles (leading dimension m+1); entries
+ *     outside the leading (m_eff+1) x m_eff block are set to zero.
+ * Sync count: LSA_MGS j+1 at step j (plus one for ||v||), LSA_CGS2 3 per step
+ * (plus one), hybrid variants 1 per step plus 1 final (plus one per fallback). */
+lsa_status lsa_arnoldi(const lsa_op* op, const double* v, int m, int variant, int precision,
+                       void* V, double* H, void* work, size_t work_bytes,
+                       lsa_stats* stats, void* stream);
+
+/* phi products y_k = phi_k(h A) v, k = 0..p (Sect. 2.2, Eq. 13 with the phi
+ * augmentation of Sect. 2.1).
+ *  v    dev, N doubles.       y  dev, (p+1) x N doubles, y + k*N = phi_k(hA)v.
+ *  p    0 <= p <= 8.          m  1 <= m <= lsa_max_m() (capped at N).
+ *  h    finite; h = 0 returns y_k = v/k!.
+ *  tol  a-posteriori check only (no substepping): LSA_NOT_CONVERGED when
+ *       err_est > tol*beta; tol <= 0 disables the check. */
+lsa_status lsa_phiv(const lsa_op* op, const double* v, double h, int p, int m, double tol,
+                    int variant, int precision, double* y, void* work, size_t work_bytes,
+                    lsa_stats* stats, void* stream);
+
+/* S5 alone: coefficients C (dev, (p+2) x m doubles, row k = phi_k(h H_m) e_1,
+ * k = 0..p+1) from one exponential of the augmented (m+p+1)-sized matrix,
+ * computed on the GPU.  H: dev, column-major with leading dimension ldh >= m. */
+lsa_status lsa_expm_phi(const double* H, int ldh, int m, double h, int p, double* C,
+                        void* work, size_t work_bytes, void* stream);
+
+/* Synchronise `stream` and read the statistics of the last call that used `work`. */
+lsa_status lsa_read_stats(const void* work, lsa_stats* out, void* stream);
+
+/* Failure-detection self-test: launches a two-block kernel whose grid barrier
+ * waits on a flag that nothing sets, with a wait limit of `seconds` (> 0,
+ * <= 10).  Expected result: LSA_ERR_TIMEOUT, with the CUDA context still usable. */
+lsa_status lsa_selftest_barrier_timeout(void* work, size_t work_bytes, double seconds, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LSARNOLDI_H */

@@ -1,0 +1,189 @@
+"""lsarnoldi for GB300: Krylov phi-function products with low-synchronisation
+Arnoldi (arXiv 2410.14917), as hand-written CUDA for sm_103a behind a C ABI.
+
+The Python layer only marshals arguments to the C entry points of
+``include/lsarnoldi.h`` (same names without the ``lsa_`` prefix) and uses
+PyTorch for device memory and streams.
+
+    import paper_2410_14917_gb300 as lsa
+    op = lsa.Operator.grayscott2d(512, 512, dx=2.5/512, Du=2e-5, Dv=1e-5, F=0.04, k=0.06,
+                                  u0=u0_cuda, v0=v0_cuda)
+    y, stats = lsa.phiv(op, v_cuda, h=1.0, p=2, m=64, variant="hcwy")
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _binding as B
+from ._binding import LsaError, LsaOp, LsaStats, PRECISIONS, VARIANTS, KINDS
+
+__all__ = ["Operator", "phiv", "arnoldi", "matvec", "expm_phi", "workspace_bytes", "read_stats",
+           "selftest_barrier_timeout", "max_m", "LsaError", "Workspace"]
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Operator:
+    """Operator descriptor; keeps the device field tensors alive."""
+
+    def __init__(self, kind, nx, ny, nz, dx, diff=0.0, diff2=0.0, vel=(0.0, 0.0, 0.0), F=0.0,
+                 k=0.0, field0=None, field1=None):
+        self.kind = kind
+        self.fields = [f for f in (field0, field1) if f is not None]
+        for f in self.fields:
+            if f.dtype != torch.float64 or not f.is_cuda or not f.is_contiguous():
+                raise ValueError("operator fields must be contiguous float64 CUDA tensors")
+        v = (list(vel) + [0.0, 0.0, 0.0])[:3]
+        self.c = LsaOp(KINDS[kind], int(nx), int(ny), int(nz), float(dx), float(diff),
+                       float(diff2), (ctypes.c_double * 3)(*v), float(F), float(k),
+                       ctypes.c_void_p(field0.data_ptr() if field0 is not None else None),
+                       ctypes.c_void_p(field1.data_ptr() if field1 is not None else None))
+
+    @property
+    def N(self) -> int:
+        n = B.lib().lsa_op_dof(ctypes.byref(self.c))
+        if n < 0:
+            raise LsaError(B.LSA_ERR_ARG, "invalid operator")
+        return int(n)
+
+    @classmethod
+    def advdiff2d(cls, nx, ny, dx, diff, vel):
+        return cls("advdiff2d", nx, ny, 1, dx, diff=diff, vel=vel)
+
+    @classmethod
+    def grayscott2d(cls, nx, ny, dx, Du, Dv, F, k, u0, v0):
+        return cls("grayscott2d", nx, ny, 1, dx, diff=Du, diff2=Dv, F=F, k=k, field0=u0, field1=v0)
+
+    @classmethod
+    def adr3d(cls, nx, ny, nz, dx, eps, vel, r):
+        return cls("adr3d", nx, ny, nz, dx, diff=eps, vel=vel, field0=r)
+
+    @classmethod
+    def from_workload(cls, cfg, fields):
+        """Build from a workload dict and a dict of float64 CUDA field tensors."""
+        kind = cfg["kind"]
+        if kind == "advdiff2d":
+            return cls.advdiff2d(cfg["nx"], cfg["ny"], cfg["dx"], cfg["diff"], cfg["vel"])
+        if kind == "grayscott2d":
+            return cls.grayscott2d(cfg["nx"], cfg["ny"], cfg["dx"], cfg["diff"], cfg["diff2"],
+                                   cfg["F"], cfg["k"], fields["u0"], fields["v0"])
+        if kind == "adr3d":
+            return cls.adr3d(cfg["nx"], cfg["ny"], cfg["nz"], cfg["dx"], cfg["diff"], cfg["vel"],
+                             fields["r"])
+        raise ValueError(kind)
+
+
+def max_m() -> int:
+    return int(B.lib().lsa_max_m())
+
+
+def workspace_bytes(op: Operator, m: int, p: int = 0, precision: str = "fp64") -> int:
+    n = B.lib().lsa_workspace_bytes(ctypes.byref(op.c), int(m), int(p), PRECISIONS[precision])
+    if n == 0:
+        raise LsaError(B.LSA_ERR_ARG, "lsa_workspace_bytes")
+    return int(n)
+
+
+class Workspace:
+    """A 256-byte aligned device buffer (torch-allocated)."""
+
+    def __init__(self, nbytes: int, device="cuda"):
+        self.nbytes = int(nbytes)
+        self.buf = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=device)
+        off = (-self.buf.data_ptr()) % 256
+        self.ptr = self.buf.data_ptr() + off
+
+    @classmethod
+    def for_call(cls, op, m, p=0, precision="fp64"):
+        return cls(workspace_bytes(op, m, p, precision))
+
+
+def _check(st, what, ok=(B.LSA_OK, B.LSA_BREAKDOWN, B.LSA_NOT_CONVERGED)):
+    if st not in ok:
+        raise LsaError(st, what)
+    return st
+
+
+def _basis_dtype(precision):
+    return torch.float64 if precision == "fp64" else torch.float32
+
+
+def matvec(op: Operator, x: torch.Tensor, precision="fp64", y=None, work=None, stream=None):
+    dt = _basis_dtype(precision)
+    if x.dtype != dt or not x.is_cuda:
+        raise ValueError(f"x must be a CUDA tensor of {dt}")
+    y = torch.empty_like(x) if y is None else y
+    work = work or Workspace.for_call(op, 1, 0, precision)
+    st = B.lib().lsa_matvec(ctypes.byref(op.c), _ptr(x), _ptr(y), PRECISIONS[precision],
+                            ctypes.c_void_p(work.ptr), work.nbytes, _stream_ptr(stream))
+    _check(st, "lsa_matvec", ok=(B.LSA_OK,))
+    return y
+
+
+def arnoldi(op: Operator, v: torch.Tensor, m: int, variant="hcwy", precision="fp64", work=None,
+            stream=None, stats=True):
+    """Returns (V, H, stats): V is N x (m+1) (column j = v_{j+1}), H is (m+1) x m."""
+    N = op.N
+    dt = _basis_dtype(precision)
+    V = torch.empty((m + 1, N), dtype=dt, device=v.device)        # column-major N x (m+1)
+    H = torch.empty((m, m + 1), dtype=torch.float64, device=v.device)  # column-major (m+1) x m
+    work = work or Workspace.for_call(op, m, 0, precision)
+    s = LsaStats()
+    st = B.lib().lsa_arnoldi(ctypes.byref(op.c), _ptr(v), int(m), VARIANTS[variant],
+                             PRECISIONS[precision], _ptr(V), _ptr(H), ctypes.c_void_p(work.ptr),
+                             work.nbytes, ctypes.byref(s) if stats else None, _stream_ptr(stream))
+    _check(st, "lsa_arnoldi")
+    return V.T, H.T, (s.as_dict() if stats else None)
+
+
+def phiv(op: Operator, v: torch.Tensor, h: float, p: int, m: int, tol: float = 0.0,
+         variant="hcwy", precision="fp64", y=None, work=None, stream=None, stats=True):
+    """y[k] = phi_k(h A) v for k = 0..p; returns (y, stats dict or None)."""
+    if v.dtype != torch.float64 or not v.is_cuda or not v.is_contiguous():
+        raise ValueError("v must be a contiguous float64 CUDA tensor")
+    N = v.numel()
+    y = torch.empty((p + 1, N), dtype=torch.float64, device=v.device) if y is None else y
+    work = work or Workspace.for_call(op, min(m, N), p, precision)
+    s = LsaStats()
+    st = B.lib().lsa_phiv(ctypes.byref(op.c), _ptr(v), float(h), int(p), int(m), float(tol),
+                          VARIANTS[variant], PRECISIONS[precision], _ptr(y),
+                          ctypes.c_void_p(work.ptr), work.nbytes,
+                          ctypes.byref(s) if stats else None, _stream_ptr(stream))
+    _check(st, "lsa_phiv")
+    return y, (s.as_dict() if stats else None)
+
+
+def expm_phi(H: torch.Tensor, m: int, h: float, p: int, stream=None):
+    """C (p+2, m): row k = phi_k(h H_m) e_1 from one exponential of the augmented matrix.
+    H: float64 CUDA tensor holding H_m in its leading m x m block (row-major torch
+    view of a column-major matrix is handled here)."""
+    Hc = H[:m, :m].T.contiguous()        # column-major storage, ldh = m
+    C = torch.empty((p + 2, m), dtype=torch.float64, device=H.device)
+    work = Workspace(1 << 20, device=H.device)
+    st = B.lib().lsa_expm_phi(_ptr(Hc), int(m), int(m), float(h), int(p), _ptr(C),
+                              ctypes.c_void_p(work.ptr), work.nbytes, _stream_ptr(stream))
+    _check(st, "lsa_expm_phi", ok=(B.LSA_OK,))
+    torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+    return C
+
+
+def read_stats(work: Workspace, stream=None):
+    s = LsaStats()
+    st = B.lib().lsa_read_stats(ctypes.c_void_p(work.ptr), ctypes.byref(s), _stream_ptr(stream))
+    return st, s.as_dict()
+
+
+def selftest_barrier_timeout(seconds: float = 0.5, stream=None) -> int:
+    work = Workspace(1 << 16)
+    return int(B.lib().lsa_selftest_barrier_timeout(ctypes.c_void_p(work.ptr), work.nbytes,
+                                                    float(seconds), _stream_ptr(stream)))

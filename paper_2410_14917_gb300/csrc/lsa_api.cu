@@ -1,0 +1,429 @@
+// C-ABI entry points of liblsarnoldi: argument checks, workspace layout and
+// the launch sequence of each call.  See include/lsarnoldi.h for the contract.
+#include <math.h>
+#include <string.h>
+
+#include "lsa_internal.cuh"
+
+namespace lsa {
+
+cudaError_t launch_arnoldi_advdiff2d(const ArnoldiParams&, int, int, cudaStream_t);
+cudaError_t launch_arnoldi_grayscott2d(const ArnoldiParams&, int, int, cudaStream_t);
+cudaError_t launch_arnoldi_adr3d(const ArnoldiParams&, int, int, cudaStream_t);
+cudaError_t launch_matvec_advdiff2d(const ArnoldiParams&, int, const void*, void*, int, cudaStream_t);
+cudaError_t launch_matvec_grayscott2d(const ArnoldiParams&, int, const void*, void*, int, cudaStream_t);
+cudaError_t launch_matvec_adr3d(const ArnoldiParams&, int, const void*, void*, int, cudaStream_t);
+int blocks_per_sm_advdiff2d(int);
+int blocks_per_sm_grayscott2d(int);
+int blocks_per_sm_adr3d(int);
+
+static const long long kTimeoutNs = 5000000000LL;   // 5 s per barrier wait
+static const double kBreakdownTolFp64 = 1e-13;
+static const double kBreakdownTolFp32 = 1e-6;
+
+bool make_devop(const lsa_op* op, DevOp* d) {
+  if (!op || !d) return false;
+  memset(d, 0, sizeof(*d));
+  if (op->nx < 1 || op->ny < 1 || op->nz < 1) return false;
+  if (!(op->dx > 0.0) || !isfinite(op->dx)) return false;
+  for (int i = 0; i < 3; ++i)
+    if (!isfinite(op->vel[i])) return false;
+  if (!isfinite(op->diff) || !isfinite(op->diff2) || !isfinite(op->F) || !isfinite(op->k)) return false;
+  d->kind = op->kind;
+  d->nx = op->nx; d->ny = op->ny; d->nz = op->nz;
+  d->npts = (long long)op->nx * op->ny * op->nz;
+  const double inv = 1.0 / (op->dx * op->dx), ih = 1.0 / op->dx;
+  switch (op->kind) {
+    case LSA_OP_ADVDIFF2D:
+      if (op->nz != 1) return false;
+      d->ns = 1;
+      d->cE = op->diff * inv - 0.5 * op->vel[0] * ih;
+      d->cW = op->diff * inv + 0.5 * op->vel[0] * ih;
+      d->cN = op->diff * inv - 0.5 * op->vel[1] * ih;
+      d->cS = op->diff * inv + 0.5 * op->vel[1] * ih;
+      d->cC = -4.0 * op->diff * inv;
+      break;
+    case LSA_OP_GRAYSCOTT2D:
+      if (op->nz != 1 || !op->field0 || !op->field1) return false;
+      d->ns = 2;
+      d->du = op->diff * inv;
+      d->dv = op->diff2 * inv;
+      d->F = op->F;
+      d->k = op->k;
+      d->f0 = op->field0;
+      d->f1 = op->field1;
+      break;
+    case LSA_OP_ADR3D: {
+      if (!op->field0) return false;
+      d->ns = 1;
+      const double e = op->diff * inv;
+      const double ux = op->vel[0], uy = op->vel[1], uz = op->vel[2];
+      d->cW = e + fmax(ux, 0.0) * ih;  d->cE = e + fmax(-ux, 0.0) * ih;
+      d->cS = e + fmax(uy, 0.0) * ih;  d->cN = e + fmax(-uy, 0.0) * ih;
+      d->cD = e + fmax(uz, 0.0) * ih;  d->cU = e + fmax(-uz, 0.0) * ih;
+      d->cC = -6.0 * e - (fabs(ux) + fabs(uy) + fabs(uz)) * ih;
+      d->f0 = op->field0;
+      break;
+    }
+    default:
+      return false;
+  }
+  d->N = d->ns * d->npts;
+  if (d->N >= (1LL << 31)) return false;   // 32-bit element offsets in the dot phase
+  return true;
+}
+
+Tiling make_tiling(const DevOp& d) {
+  Tiling t;
+  t.tiles_x = (d.nx + TX - 1) / TX;
+  t.tiles_y = (d.ny + TY - 1) / TY;
+  t.ZS = (d.kind == LSA_OP_ADR3D) ? (d.nz < 32 ? d.nz : 32) : 1;
+  t.zsegs = (d.nz + t.ZS - 1) / t.ZS;
+  t.ntiles = t.tiles_x * t.tiles_y * t.zsegs;
+  return t;
+}
+
+static int sm_count() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  return sms;
+}
+
+int arnoldi_blocks_per_sm(const DevOp& d, int precision) {
+  static int cache[4][2][16];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 16) dev = 0;
+  int& c = cache[d.kind][precision][dev];
+  if (c > 0) return c;
+  int nb = 0;
+  if (d.kind == LSA_OP_ADVDIFF2D) nb = blocks_per_sm_advdiff2d(precision);
+  else if (d.kind == LSA_OP_GRAYSCOTT2D) nb = blocks_per_sm_grayscott2d(precision);
+  else nb = blocks_per_sm_adr3d(precision);
+  c = nb;
+  return nb;
+}
+
+cudaError_t launch_arnoldi(const ArnoldiParams& P, int precision, int G, cudaStream_t s) {
+  if (P.op.kind == LSA_OP_ADVDIFF2D) return launch_arnoldi_advdiff2d(P, precision, G, s);
+  if (P.op.kind == LSA_OP_GRAYSCOTT2D) return launch_arnoldi_grayscott2d(P, precision, G, s);
+  return launch_arnoldi_adr3d(P, precision, G, s);
+}
+
+cudaError_t launch_matvec(const ArnoldiParams& P, int precision, const void* x, void* y, int G,
+                          cudaStream_t s) {
+  if (P.op.kind == LSA_OP_ADVDIFF2D) return launch_matvec_advdiff2d(P, precision, x, y, G, s);
+  if (P.op.kind == LSA_OP_GRAYSCOTT2D) return launch_matvec_grayscott2d(P, precision, x, y, G, s);
+  return launch_matvec_adr3d(P, precision, x, y, G, s);
+}
+
+// Workspace layout for (op, m, precision).  G = CTAs of the persistent kernel.
+static bool make_layout(const DevOp& d, int m, int precision, Layout* L) {
+  const int sms = sm_count();
+  if (sms <= 0) return false;
+  const int bps = arnoldi_blocks_per_sm(d, precision);
+  if (bps <= 0) return false;
+  const Tiling t = make_tiling(d);
+  int G = sms * bps;
+  if (G > t.ntiles) G = t.ntiles;
+  if (G < 1) G = 1;
+  const size_t bsz = precision == LSA_FP64 ? 8 : 4;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
+  L->ctl = take(sizeof(Ctl));
+  L->partials = take((size_t)sms * bps * SLOTS * sizeof(double));
+  L->T = take((size_t)MMAX * MMAX * sizeof(double));
+  L->L = take((size_t)MMAX * MMAX * sizeof(double));
+  L->H = take((size_t)(m + 1) * m * sizeof(double));
+  L->V = take((size_t)d.N * (m + 1) * bsz);
+  L->W0 = take((size_t)d.N * bsz);
+  L->W1 = take((size_t)d.N * bsz);
+  L->small = take((size_t)6 * SMALL_STRIDE * SMALL_STRIDE * sizeof(double));
+  L->coefs = take((size_t)(PMAX + 2) * (MMAX + 2) * sizeof(double));
+  size_t nfield = 0;
+  if (precision == LSA_FP32_BASIS) {
+    if (d.kind == LSA_OP_GRAYSCOTT2D) nfield = (size_t)d.nx * d.ny;
+    else if (d.kind == LSA_OP_ADR3D) nfield = (size_t)d.npts;
+  }
+  L->g0 = take(nfield * sizeof(float));
+  L->g1 = take(nfield * sizeof(float));
+  L->total = off;
+  L->G = G;
+  return true;
+}
+
+static lsa_status from_cuda(cudaError_t e) { return e == cudaSuccess ? LSA_OK : LSA_ERR_CUDA; }
+
+static lsa_status fill_stats(const void* work, lsa_stats* out, cudaStream_t s) {
+  Ctl c;
+  cudaError_t e = cudaMemcpyAsync(&c, work, sizeof(Ctl), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return LSA_ERR_CUDA;
+  if (out) {
+    out->status = c.status;
+    out->m_eff = c.m_eff;
+    out->breakdown = c.breakdown;
+    out->norm_fallbacks = c.fallbacks;
+    out->grid_syncs = c.syncs;
+    out->grid_barriers = c.barriers;
+    out->beta = c.beta;
+    out->err_est = c.err_est;
+    out->h_last = c.h_last;
+    out->ms_arnoldi = out->ms_expm = out->ms_combine = 0.f;
+    out->launches = 0;
+  }
+  if (c.status < 0) return (lsa_status)c.status;
+  if (c.breakdown) return LSA_BREAKDOWN;
+  return (lsa_status)c.status;
+}
+
+static bool aligned256(const void* p) { return ((uintptr_t)p & 255u) == 0; }
+
+// CUDA events around the kernels of one call, used only when the caller asks
+// for statistics (the call synchronises then anyway).
+struct CallTimer {
+  bool on = false;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaStream_t s = nullptr;
+  CallTimer(bool enable, cudaStream_t st) : on(enable), s(st) {
+    if (!on) return;
+    for (auto& e : ev)
+      if (cudaEventCreate(&e) != cudaSuccess) { on = false; e = nullptr; }
+  }
+  void mark(int i) { if (on) cudaEventRecord(ev[i], s); }
+  float ms(int a, int b) {
+    float t = 0.f;
+    if (on) cudaEventElapsedTime(&t, ev[a], ev[b]);
+    return t;
+  }
+  ~CallTimer() {
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
+  }
+};
+
+struct Prepared {
+  DevOp d;
+  Layout L;
+  ArnoldiParams P;
+  char* w;
+};
+
+static lsa_status prepare(const lsa_op* op, int m, int precision, void* work, size_t work_bytes,
+                          Prepared* pr) {
+  if (precision != LSA_FP64 && precision != LSA_FP32_BASIS) return LSA_ERR_ARG;
+  if (!make_devop(op, &pr->d)) return LSA_ERR_ARG;
+  if (m < 1 || m > MMAX) return LSA_ERR_ARG;
+  if (!make_layout(pr->d, m, precision, &pr->L)) return LSA_ERR_CUDA;
+  if (!work || !aligned256(work) || work_bytes < pr->L.total) return LSA_ERR_WORKSPACE;
+  pr->w = (char*)work;
+  if (precision == LSA_FP32_BASIS) {
+    pr->d.g0 = (const float*)(pr->w + pr->L.g0);
+    pr->d.g1 = (const float*)(pr->w + pr->L.g1);
+  }
+  ArnoldiParams& P = pr->P;
+  memset(&P, 0, sizeof(P));
+  P.op = pr->d;
+  P.tl = make_tiling(pr->d);
+  P.ctl = (Ctl*)(pr->w + pr->L.ctl);
+  P.partials = (double*)(pr->w + pr->L.partials);
+  P.T = (double*)(pr->w + pr->L.T);
+  P.L = (double*)(pr->w + pr->L.L);
+  P.V = pr->w + pr->L.V;
+  P.W0 = pr->w + pr->L.W0;
+  P.W1 = pr->w + pr->L.W1;
+  P.H = (double*)(pr->w + pr->L.H);
+  P.m = m;
+  P.brk_tol = precision == LSA_FP64 ? kBreakdownTolFp64 : kBreakdownTolFp32;
+  P.timeout_ns = kTimeoutNs;
+  return LSA_OK;
+}
+
+}  // namespace lsa
+
+using namespace lsa;
+
+extern "C" {
+
+int lsa_max_m(void) { return MMAX; }
+int lsa_version(void) { return 100; }
+
+const char* lsa_status_string(int s) {
+  switch (s) {
+    case LSA_OK: return "LSA_OK";
+    case LSA_BREAKDOWN: return "LSA_BREAKDOWN";
+    case LSA_NOT_CONVERGED: return "LSA_NOT_CONVERGED";
+    case LSA_ERR_ARG: return "LSA_ERR_ARG";
+    case LSA_ERR_CUDA: return "LSA_ERR_CUDA";
+    case LSA_ERR_TIMEOUT: return "LSA_ERR_TIMEOUT";
+    case LSA_ERR_NUMERIC: return "LSA_ERR_NUMERIC";
+    case LSA_ERR_WORKSPACE: return "LSA_ERR_WORKSPACE";
+    default: return "LSA_UNKNOWN";
+  }
+}
+
+long long lsa_op_dof(const lsa_op* op) {
+  DevOp d;
+  if (!make_devop(op, &d)) return -1;
+  return d.N;
+}
+
+size_t lsa_workspace_bytes(const lsa_op* op, int m, int p, int precision) {
+  DevOp d;
+  if (precision != LSA_FP64 && precision != LSA_FP32_BASIS) return 0;
+  if (!make_devop(op, &d) || m < 1 || m > MMAX || p < 0 || p > PMAX) return 0;
+  Layout L;
+  if (!make_layout(d, m, precision, &L)) return 0;
+  return L.total;
+}
+
+lsa_status lsa_matvec(const lsa_op* op, const void* x, void* y, int precision, void* work,
+                      size_t work_bytes, void* stream) {
+  if (!x || !y) return LSA_ERR_ARG;
+  Prepared pr;
+  lsa_status st = prepare(op, 1, precision, work, work_bytes, &pr);
+  if (st != LSA_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = launch_init(pr.P.ctl, pr.d, (float*)pr.d.g0, (float*)pr.d.g1, precision, nullptr, 0, s);
+  if (e == cudaSuccess) e = launch_matvec(pr.P, precision, x, y, pr.L.G, s);
+  return from_cuda(e);
+}
+
+lsa_status lsa_arnoldi(const lsa_op* op, const double* v, int m, int variant, int precision,
+                       void* V, double* H, void* work, size_t work_bytes, lsa_stats* stats,
+                       void* stream) {
+  if (!v || !V || !H) return LSA_ERR_ARG;
+  if (variant < LSA_MGS || variant > LSA_HGSMGS) return LSA_ERR_ARG;
+  long long N = lsa_op_dof(op);
+  if (N < 1 || m > N) return LSA_ERR_ARG;
+  Prepared pr;
+  lsa_status st = prepare(op, m, precision, work, work_bytes, &pr);
+  if (st != LSA_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  ArnoldiParams P = pr.P;
+  P.vin = v;
+  P.V = V;
+  P.H = H;
+  P.variant = variant;
+  P.write_vlast = 1;
+  CallTimer tm(stats != nullptr, s);
+  cudaError_t e = launch_init(P.ctl, pr.d, (float*)pr.d.g0, (float*)pr.d.g1, precision, H,
+                              (m + 1) * m, s);
+  tm.mark(0);
+  if (e == cudaSuccess) e = launch_arnoldi(P, precision, pr.L.G, s);
+  tm.mark(1);
+  if (e == cudaSuccess && variant >= LSA_HCWY) e = launch_scale_basis(V, precision, N, m, P.ctl, s);
+  if (e != cudaSuccess) return LSA_ERR_CUDA;
+  if (stats) {
+    lsa_status r = fill_stats(P.ctl, stats, s);
+    stats->ms_arnoldi = tm.ms(0, 1);
+    stats->launches = variant >= LSA_HCWY ? 3 : 2;
+    return r;
+  }
+  return LSA_OK;
+}
+
+lsa_status lsa_phiv(const lsa_op* op, const double* v, double h, int p, int m, double tol,
+                    int variant, int precision, double* y, void* work, size_t work_bytes,
+                    lsa_stats* stats, void* stream) {
+  if (!v || !y) return LSA_ERR_ARG;
+  if (variant < LSA_MGS || variant > LSA_HGSMGS) return LSA_ERR_ARG;
+  if (p < 0 || p > PMAX || !isfinite(h) || isnan(tol)) return LSA_ERR_ARG;
+  long long N = lsa_op_dof(op);
+  if (N < 1 || m < 1) return LSA_ERR_ARG;
+  if (m > N) m = (int)N;
+  Prepared pr;
+  lsa_status st = prepare(op, m, precision, work, work_bytes, &pr);
+  if (st != LSA_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  ArnoldiParams P = pr.P;
+  P.vin = v;
+  P.variant = variant;
+  P.write_vlast = 0;
+  CallTimer tm(stats != nullptr, s);
+  cudaError_t e = launch_init(P.ctl, pr.d, (float*)pr.d.g0, (float*)pr.d.g1, precision, P.H,
+                              (m + 1) * m, s);
+  tm.mark(0);
+  if (e == cudaSuccess) e = launch_arnoldi(P, precision, pr.L.G, s);
+  tm.mark(1);
+  if (e == cudaSuccess) {
+    SmallParams S;
+    memset(&S, 0, sizeof(S));
+    S.H = P.H;
+    S.ldh = m + 1;
+    S.ctl_in = P.ctl;
+    S.ctl = P.ctl;
+    S.m = m;
+    S.p = p;
+    S.h = h;
+    S.mats = (double*)(pr.w + pr.L.small);
+    S.C = (double*)(pr.w + pr.L.coefs);
+    S.ldc = MMAX + 2;
+    S.scale_out = 1;
+    S.timeout_ns = kTimeoutNs;
+    S.tol = tol;
+    e = launch_expm(S, s);
+    tm.mark(2);
+    if (e == cudaSuccess)
+      e = launch_combine(P.V, precision, N, S.C, S.ldc, p, P.ctl, y, s);
+    tm.mark(3);
+  }
+  if (e != cudaSuccess) return LSA_ERR_CUDA;
+  if (stats) {
+    lsa_status r = fill_stats(P.ctl, stats, s);
+    stats->ms_arnoldi = tm.ms(0, 1);
+    stats->ms_expm = tm.ms(1, 2);
+    stats->ms_combine = tm.ms(2, 3);
+    stats->launches = 4;
+    return r;
+  }
+  return LSA_OK;
+}
+
+lsa_status lsa_expm_phi(const double* H, int ldh, int m, double h, int p, double* C, void* work,
+                        size_t work_bytes, void* stream) {
+  if (!H || !C || m < 1 || m > MMAX || ldh < m || p < 0 || p > PMAX || !isfinite(h))
+    return LSA_ERR_ARG;
+  size_t need = align256(sizeof(Ctl)) + (size_t)6 * SMALL_STRIDE * SMALL_STRIDE * sizeof(double);
+  if (!work || !aligned256(work) || work_bytes < need) return LSA_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  Ctl* ctl = (Ctl*)work;
+  cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(Ctl), s);
+  SmallParams S;
+  memset(&S, 0, sizeof(S));
+  S.H = H;
+  S.ldh = ldh;
+  S.ctl_in = nullptr;
+  S.ctl = ctl;
+  S.m = m;
+  S.p = p;
+  S.h = h;
+  S.mats = (double*)((char*)work + align256(sizeof(Ctl)));
+  S.C = C;
+  S.ldc = m;
+  S.scale_out = 0;
+  S.timeout_ns = kTimeoutNs;
+  if (e == cudaSuccess) e = launch_expm(S, s);
+  return from_cuda(e);
+}
+
+lsa_status lsa_read_stats(const void* work, lsa_stats* out, void* stream) {
+  if (!work) return LSA_ERR_ARG;
+  return fill_stats(work, out, (cudaStream_t)stream);
+}
+
+lsa_status lsa_selftest_barrier_timeout(void* work, size_t work_bytes, double seconds,
+                                        void* stream) {
+  if (!work || !aligned256(work) || work_bytes < sizeof(Ctl)) return LSA_ERR_WORKSPACE;
+  if (!(seconds > 0.0) || seconds > 10.0) return LSA_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  Ctl* ctl = (Ctl*)work;
+  cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(Ctl), s);
+  if (e == cudaSuccess) e = launch_timeout_selftest(ctl, (long long)(seconds * 1e9), s);
+  if (e != cudaSuccess) return LSA_ERR_CUDA;
+  lsa_stats st;
+  return fill_stats(ctl, &st, s);
+}
+
+}  // extern "C"

@@ -1,0 +1,836 @@
+// Persistent Arnoldi kernels: the tile pass engine and the three Gram-Schmidt
+// schemes (MGS, CGS2, hybrid low-synchronisation) built on it.
+//
+// One cooperative launch runs a whole Arnoldi process.  Each "pass" streams
+// the grid tile by tile: it projects a vector (x = a*src - sum_c coef_c V_c),
+// optionally applies the stencil (w = A x, needing the projection on a
+// one-point halo, recomputed redundantly by each tile), and accumulates inner
+// products of basis columns with x and/or w.  The per-CTA partial sums go to
+// global memory, and one grid barrier reduces them: the CTA that arrives last
+// sums the partials in a fixed order (deterministic) and does the small
+// O(j^2) double-precision work of the step (H column, correction matrix T,
+// norm estimate) before releasing the others.  A global reduction of the paper
+// (an MPI_Allreduce, Sect. 2.3) is therefore one grid barrier here.
+#pragma once
+
+#include "lsa_ops.cuh"
+
+namespace lsa {
+
+enum : int { DOT_X = 1, DOT_W = 2 };
+enum : int { SELF_XX = 1, SELF_XW = 2, SELF_WW = 4 };
+
+template <class B>
+struct PassT {
+  int c0, c1;            // projection columns [c0, c1) of V (coefficients in smem coef[c])
+  double a;              // scale of the source vector
+  const double* src64;   // source: fp64 start vector (first pass) ...
+  const B* srcB;         // ... or a basis-typed buffer (may alias xout: in-place update)
+  B* xout;               // destination of x (owned interior points), or null
+  B* wout;               // stencil output (w = A x), null when the pass has no stencil
+  int d0, d1;            // dot columns [d0, d1) of V
+  int dmode;             // DOT_X | DOT_W
+  int self;              // SELF_* bits
+};
+
+__device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+template <class Op, class Tc, class B>
+struct Engine {
+  static constexpr int NS = Op::NS;
+  static constexpr int DIM = Op::DIM;
+  static constexpr int RING = (DIM == 3) ? 3 : 1;
+  static constexpr int NPL = (NS * TX * TY + 31) / 32;
+  static constexpr bool F64 = sizeof(Tc) == 8;
+
+  struct Smem {
+    Tc ring[RING * NS * PS];
+    Tc wbuf[NS * TX * TY];
+    Tc coefc[MMAX + 2];
+    double red[SLOTS];
+    double tmp[4][MMAX + 2];
+    double small[MMAX * MMAX];
+    double bred[NW][3];
+    double sj, scale, true_nrm, ss;
+    Tc a;
+    int flag, done, fallback_pending, stop;
+  };
+
+  const ArnoldiParams& P;
+  Smem& S;
+  Coef<Tc> cf;
+  const int tid, lane, warp;
+  // dot accumulators (per lane)
+  double ax[KMAX], aw[KMAX];
+  float axs[KMAX], axc[KMAX], aws[KMAX], awc[KMAX];
+  double sxx, sxw, sww;
+
+  __device__ Engine(const ArnoldiParams& p, Smem& s)
+      : P(p), S(s), tid(threadIdx.x), lane(threadIdx.x & 31), warp(threadIdx.x >> 5) {
+    cf.load(P.op);
+  }
+
+  __device__ __forceinline__ const B* Vc(int c) const {
+    return reinterpret_cast<const B*>(P.V) + (long long)c * P.op.N;
+  }
+
+  __device__ void zero_acc() {
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) { ax[k] = 0; aw[k] = 0; axs[k] = 0; axc[k] = 0; aws[k] = 0; awc[k] = 0; }
+    sxx = sxw = sww = 0;
+  }
+
+  __device__ __forceinline__ static void kahan(float& s, float& c, float v) {
+    float y = v - c;
+    float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+
+  __device__ __forceinline__ int slot(int z) const { return RING == 1 ? 0 : (z + 3) % 3; }
+
+  // Project plane z (wrapped) of the tile into ring slot `sl`.  With `halo`,
+  // the projection also covers the four one-point halo strips.  `own`: the
+  // plane's interior belongs to this tile (stores and self terms happen).
+  __device__ void project_plane(const PassT<B>& ps, int x0, int y0, int z, int w, int hg, int sl,
+                                bool halo, bool own) {
+    constexpr int QP = (NS * (TX * TY + 2 * TX + 2 * TY) + NT - 1) / NT;  // points per thread
+    const DevOp& d = P.op;
+    const int zw = wrapi(z, d.nz);
+    const int pint = w * hg;
+    const int pall = halo ? pint + 2 * w + 2 * hg : pint;
+    const int total = NS * pall;
+    const long long N = d.N;
+    const B* Vb = reinterpret_cast<const B*>(P.V);
+    Tc* ring = S.ring + sl * NS * PS;
+    const Tc a = (Tc)ps.a;
+    int gi[QP], so[QP];
+    Tc x[QP];
+#pragma unroll
+    for (int u = 0; u < QP; ++u) {
+      const int q = tid + u * NT;
+      gi[u] = 0;
+      so[u] = -1;
+      x[u] = (Tc)0;
+      if (q < total) {
+        int s = q / pall;
+        int r = q - s * pall;
+        int lx, ly;
+        if (r < pint) { ly = r / w; lx = r - ly * w; }
+        else {
+          int h = r - pint;
+          if (h < w) { lx = h; ly = -1; }
+          else if (h < 2 * w) { lx = h - w; ly = hg; }
+          else if (h < 2 * w + hg) { lx = -1; ly = h - 2 * w; }
+          else { lx = w; ly = h - 2 * w - hg; }
+        }
+        int gx = wrapi(x0 + lx, d.nx), gy = wrapi(y0 + ly, d.ny);
+        gi[u] = (int)(s * d.npts + gx + (long long)d.nx * (gy + (long long)d.ny * zw));
+        so[u] = s * PS + (ly + 1) * PW + lx + 1;
+        if (r < pint && own) so[u] |= (1 << 30);   // owned interior point
+        if (ps.src64) x[u] = a * (Tc)__ldg(ps.src64 + gi[u]);
+        else x[u] = a * (Tc)__ldcg(ps.srcB + gi[u]);
+      }
+    }
+    // x -= sum_c coef_c V_c : one coefficient load per column, applied to all points
+    int c = ps.c0;
+    for (; c + 2 <= ps.c1; c += 2) {
+      const Tc c0 = S.coefc[c], c1 = S.coefc[c + 1];
+      const B* col0 = Vb + (long long)c * N;
+      const B* col1 = col0 + N;
+      Tc v0[QP], v1[QP];
+#pragma unroll
+      for (int u = 0; u < QP; ++u) { v0[u] = (Tc)__ldcg(col0 + gi[u]); v1[u] = (Tc)__ldcg(col1 + gi[u]); }
+#pragma unroll
+      for (int u = 0; u < QP; ++u) { x[u] = fma(-c0, v0[u], x[u]); x[u] = fma(-c1, v1[u], x[u]); }
+    }
+    if (c < ps.c1) {
+      const Tc c0 = S.coefc[c];
+      const B* col0 = Vb + (long long)c * N;
+#pragma unroll
+      for (int u = 0; u < QP; ++u) x[u] = fma(-c0, (Tc)__ldcg(col0 + gi[u]), x[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < QP; ++u) {
+      if (so[u] < 0) continue;
+      Tc xv = x[u];
+      if constexpr (!F64) xv = (Tc)(B)xv;   // the stencil sees exactly the stored value
+      ring[so[u] & ((1 << 30) - 1)] = xv;
+      if (so[u] & (1 << 30)) {
+        if (ps.xout) ps.xout[gi[u]] = (B)xv;
+        if (!ps.wout && (ps.self & SELF_XX)) sxx += (double)xv * (double)xv;
+      }
+    }
+  }
+
+  // Stencil at plane z (interior only) from the ring: w = A x.
+  __device__ void stencil_plane(const PassT<B>& ps, int x0, int y0, int z, int w, int hg) {
+    const DevOp& d = P.op;
+    if (tid >= w * hg) return;
+    int ly = tid / w, lx = tid - ly * w;
+    const Tc* zm = S.ring + slot(z - 1) * NS * PS;
+    const Tc* z0 = S.ring + slot(z) * NS * PS;
+    const Tc* zp = S.ring + slot(z + 1) * NS * PS;
+    int o = (ly + 1) * PW + lx + 1;
+    long long gpt = (x0 + lx) + (long long)d.nx * ((y0 + ly) + (long long)d.ny * z);
+    Tc out[NS];
+    Op::template apply<Tc>(d, cf, zm, z0, zp, o, gpt, out);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      Tc wv = out[s];
+      if constexpr (!F64) wv = (Tc)(B)wv;
+      S.wbuf[s * TX * TY + tid] = wv;
+      ps.wout[s * d.npts + gpt] = (B)wv;
+      double xd = (double)z0[s * PS + o], wd = (double)wv;
+      if (ps.self & SELF_XX) sxx += xd * xd;
+      if (ps.self & SELF_XW) sxw += xd * wd;
+      if (ps.self & SELF_WW) sww += wd * wd;
+    }
+  }
+
+  // Inner products of basis columns [d0, d1) with the plane's x and/or w:
+  // warp <-> columns, lane <-> interior points.
+  __device__ void dots_plane(const PassT<B>& ps, int x0, int y0, int z, int w, int hg, int sl) {
+    if (ps.d1 <= ps.d0) return;
+    const DevOp& d = P.op;
+    const int pint = w * hg;
+    const int count = NS * pint;
+    const Tc* xr = S.ring + sl * NS * PS;
+    Tc xv[NPL], wv[NPL];
+    int gi[NPL];
+#pragma unroll
+    for (int k = 0; k < NPL; ++k) {
+      int ql = lane + 32 * k;
+      if (ql < count) {
+        int s = ql / pint, q = ql - s * pint;
+        int ly = q / w, lx = q - ly * w;
+        xv[k] = xr[s * PS + (ly + 1) * PW + lx + 1];
+        wv[k] = (ps.dmode & DOT_W) ? S.wbuf[s * TX * TY + q] : (Tc)0;
+        gi[k] = (int)(s * d.npts + (x0 + lx) + (long long)d.nx * ((y0 + ly) + (long long)d.ny * z));
+      } else {
+        xv[k] = 0; wv[k] = 0; gi[k] = 0;
+      }
+    }
+    const bool dx = ps.dmode & DOT_X, dw = ps.dmode & DOT_W;
+#pragma unroll
+    for (int kk = 0; kk < KMAX; ++kk) {
+      int c = ps.d0 + warp + NW * kk;
+      if (c < ps.d1) {
+        const B* base = Vc(c);
+        if constexpr (F64) {
+          double px = 0, pw = 0;
+#pragma unroll
+          for (int k = 0; k < NPL; ++k) {
+            double v = (double)__ldcg(base + gi[k]);
+            px = fma(v, (double)xv[k], px);
+            pw = fma(v, (double)wv[k], pw);
+          }
+          if (dx) ax[kk] += px;
+          if (dw) aw[kk] += pw;
+        } else {
+          float px = 0.f, pw = 0.f;
+#pragma unroll
+          for (int k = 0; k < NPL; ++k) {
+            float v = (float)__ldcg(base + gi[k]);
+            px = fmaf(v, (float)xv[k], px);
+            pw = fmaf(v, (float)wv[k], pw);
+          }
+          if (dx) kahan(axs[kk], axc[kk], px);
+          if (dw) kahan(aws[kk], awc[kk], pw);
+        }
+      }
+    }
+  }
+
+  // One pass over all tiles of this CTA; writes the CTA's partial sums.
+  // Returns the number of reduction slots used.
+  __device__ int run_pass(const PassT<B>& ps) {
+    const DevOp& d = P.op;
+    const Tiling& tl = P.tl;
+    zero_acc();
+    const bool stencil = ps.wout != nullptr;
+    for (int t = blockIdx.x; t < tl.ntiles; t += gridDim.x) {
+      int bx = t % tl.tiles_x;
+      int rr = t / tl.tiles_x;
+      int by = rr % tl.tiles_y;
+      int bz = rr / tl.tiles_y;
+      int x0 = bx * TX, y0 = by * TY, z0 = bz * tl.ZS;
+      int w = min(TX, d.nx - x0), hg = min(TY, d.ny - y0), zl = min(tl.ZS, d.nz - z0);
+      if (DIM == 3 && stencil) {
+        project_plane(ps, x0, y0, z0 - 1, w, hg, slot(z0 - 1), false, false);
+        project_plane(ps, x0, y0, z0, w, hg, slot(z0), true, true);
+        for (int z = z0; z < z0 + zl; ++z) {
+          bool inside = (z + 1 < z0 + zl);
+          project_plane(ps, x0, y0, z + 1, w, hg, slot(z + 1), inside, inside);
+          __syncthreads();
+          stencil_plane(ps, x0, y0, z, w, hg);
+          __syncthreads();
+          dots_plane(ps, x0, y0, z, w, hg, slot(z));
+        }
+        __syncthreads();
+      } else {
+        for (int z = z0; z < z0 + zl; ++z) {
+          project_plane(ps, x0, y0, z, w, hg, 0, stencil, true);
+          __syncthreads();
+          if (stencil) {
+            stencil_plane(ps, x0, y0, z, w, hg);
+            __syncthreads();
+          }
+          dots_plane(ps, x0, y0, z, w, hg, 0);
+          __syncthreads();
+        }
+      }
+    }
+    // write this CTA's partials
+    const int nd = ps.d1 > ps.d0 ? ps.d1 - ps.d0 : 0;
+    double* part = P.partials + (long long)blockIdx.x * SLOTS;
+#pragma unroll
+    for (int kk = 0; kk < KMAX; ++kk) {
+      int c = ps.d0 + warp + NW * kk;
+      double vx, vw;
+      if constexpr (F64) { vx = ax[kk]; vw = aw[kk]; }
+      else { vx = (double)axs[kk] - (double)axc[kk]; vw = (double)aws[kk] - (double)awc[kk]; }
+      vx = warp_sum(vx);
+      vw = warp_sum(vw);
+      if (c < ps.d1 && lane == 0) {
+        part[c - ps.d0] = (ps.dmode & DOT_X) ? vx : 0.0;
+        part[nd + c - ps.d0] = (ps.dmode & DOT_W) ? vw : 0.0;
+      }
+    }
+    double a0 = warp_sum(sxx), a1 = warp_sum(sxw), a2 = warp_sum(sww);
+    if (lane == 0) { S.bred[warp][0] = a0; S.bred[warp][1] = a1; S.bred[warp][2] = a2; }
+    __syncthreads();
+    if (tid < 3) {
+      double acc = 0;
+      for (int i = 0; i < NW; ++i) acc += S.bred[i][tid];
+      part[2 * nd + tid] = acc;
+    }
+    return 2 * nd + 3;
+  }
+
+  // Last CTA: fixed-order reduction of all CTAs' partials into S.red.
+  __device__ void reduce_partials(int nslots) {
+    const int G = gridDim.x;
+    for (int s = tid; s < nslots; s += NT) {
+      double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+      int c = 0;
+      for (; c + 4 <= G; c += 4) {
+        a0 += __ldcg(P.partials + (long long)c * SLOTS + s);
+        a1 += __ldcg(P.partials + (long long)(c + 1) * SLOTS + s);
+        a2 += __ldcg(P.partials + (long long)(c + 2) * SLOTS + s);
+        a3 += __ldcg(P.partials + (long long)(c + 3) * SLOTS + s);
+      }
+      for (; c < G; ++c) a0 += __ldcg(P.partials + (long long)c * SLOTS + s);
+      S.red[s] = (a0 + a1) + (a2 + a3);
+    }
+    __syncthreads();
+  }
+
+  // Read the published control state into shared memory (all threads).
+  __device__ void load_ctl(int ncoef) {
+    for (int c = tid; c < ncoef; c += NT) S.coefc[c] = (Tc)__ldcg(&P.ctl->coef[c]);
+    if (tid == 0) {
+      S.a = (Tc)__ldcg(&P.ctl->a);
+      S.done = __ldcg(&P.ctl->done);
+      S.fallback_pending = __ldcg(&P.ctl->fallback_pending);
+    }
+    __syncthreads();
+  }
+
+  // Barrier + reduction; `fn` runs in the last CTA with S.red filled.
+  template <class Fn>
+  __device__ bool reduce_step(unsigned& gen, int nslots, int ncoef_after, Fn fn) {
+    const BarrierRef br = arnoldi_barrier(P.ctl);
+    int r = barrier_arrive(br, gen, gridDim.x, &S.flag, P.timeout_ns);
+    if (r < 0) return false;
+    if (r == 1) {
+      reduce_partials(nslots);
+      fn();
+      __syncthreads();
+      if (tid == 0) { P.ctl->barriers += 1; }
+      barrier_release(br, gen);
+    }
+    ++gen;
+    load_ctl(ncoef_after);
+    return true;
+  }
+
+  __device__ __forceinline__ double& Hat(int r, int c) const { return P.H[r + (long long)c * (P.m + 1)]; }
+
+  // -------------------------------------------------------------------------
+  // Hybrid low-synchronisation step (Alg. 4 with Alg. 5/6/7), last CTA only.
+  // S.red: x_i.x_j (i < j-1), x_i.w_j (i < j-1), x_j.x_j, x_j.w_j, w_j.w_j for the
+  // stored (estimate-normalised) x and w = A x.
+  __device__ void hybrid_step(int j) {
+    Ctl* ctl = P.ctl;
+    const int np = j - 1;
+    double* temp1 = S.tmp[0];
+    double* temp2 = S.tmp[1];
+    double* hcol = S.tmp[2];
+    double* aux = S.tmp[3];
+    if (tid == 0) {
+      double Gj = S.red[2 * np], Pj = S.red[2 * np + 1], Q = S.red[2 * np + 2];
+      S.flag = 0;
+      if (j == 1 && Gj == 0.0) {              // zero start vector: y = 0
+        ctl->beta = 0.0;
+        ctl->m_eff = 0;
+        ctl->done = 1;
+        S.flag = 1;
+      } else if (!(Gj > 0.0) || !isfinite(Gj) || !isfinite(Pj) || !isfinite(Q)) {
+        ctl->status = (int)LSA_ERR_NUMERIC;
+        ctl->done = 1;
+        ctl->m_eff = j - 1;
+        S.flag = 1;
+      } else {
+        double sj = 1.0 / sqrt(Gj);
+        S.sj = sj;
+        if (j == 1) {
+          ctl->beta = sqrt(Gj);
+        } else {
+          double tn = ctl->nrm_est * sqrt(Gj);   // true norm of the previous vector
+          S.true_nrm = tn;
+          if (!(tn > P.brk_tol * ctl->aw_prev)) { // lagged breakdown test
+            Hat(j - 1, j - 2) = tn;
+            ctl->m_eff = j - 1;
+            ctl->breakdown = 1;
+            ctl->done = 1;
+            S.flag = 1;
+          }
+        }
+        ctl->sigma[j - 1] = sj;
+        temp2[np] = sj * sj * Pj;
+        temp2[np + 1] = sj * sj * Q;
+      }
+      ctl->syncs += 1;
+    }
+    __syncthreads();
+    if (S.flag) return;
+    for (int i = tid; i < np; i += NT) {
+      double si = __ldcg(&ctl->sigma[i]);
+      temp1[i] = si * S.sj * S.red[i];
+      temp2[i] = si * S.sj * S.red[np + i];
+    }
+    __syncthreads();
+    if (j == 1) {
+      if (tid == 0) hcol[0] = temp2[0];
+    } else {
+      // New row of T (Alg. 5: T_{j,1:j-1} = -temp_{1:j-1,1}^T T_{1:j-1,1:j-1};
+      // Alg. 6: T_{j,1:j-1} = -temp_{1:j-1,1}^T; for Alg. 7 this is M^{-1}).
+      stage(P.T, np);
+      for (int k = tid; k < np; k += NT) {
+        double acc = -temp1[k];
+        if (P.variant != LSA_HNCWY)
+          for (int i = k + 1; i < np; ++i) acc = fma(-temp1[i], S.small[i * MMAX + k], acc);
+        S.small[np * MMAX + k] = acc;
+        P.T[np * MMAX + k] = acc;
+      }
+      __syncthreads();
+      if (P.variant != LSA_HGSMGS) {
+        apply_unit_lower(temp2, hcol, j);                 // H_{1:j,j} = T_j temp_{1:j,2}
+      } else {
+        // Alg. 7: y = M^{-1} temp2; p = (I + N M^{-1}) temp2 = temp2 - L^T y;
+        // H_{1:j,j} solves (I + L) x = p.
+        apply_unit_lower(temp2, aux, j);                  // aux = y
+        stage(P.L, np);
+        for (int k = tid; k < np; k += NT) {
+          S.small[np * MMAX + k] = temp1[k];
+          P.L[np * MMAX + k] = temp1[k];
+        }
+        __syncthreads();
+        for (int r = tid; r < j; r += NT) {
+          double acc = 0.0;
+          for (int k = r + 1; k < j; ++k) acc = fma(S.small[k * MMAX + r], aux[k], acc);
+          hcol[r] = temp2[r] - acc;
+        }
+        __syncthreads();
+        if (warp == 0) {                                   // forward substitution
+          for (int r = 0; r < j; ++r) {
+            double acc = 0.0;
+            for (int k = lane; k < r; k += 32) acc = fma(S.small[r * MMAX + k], hcol[k], acc);
+            acc = warp_sum(acc);
+            if (lane == 0) hcol[r] = hcol[r] - acc;
+            __syncwarp();
+          }
+        }
+      }
+    }
+    __syncthreads();
+    for (int r = tid; r < j; r += NT) Hat(r, j - 1) = hcol[r];
+    if (warp == 0) {
+      double ss = 0.0;
+      for (int i = lane; i < j; i += 32) ss = fma(temp2[i], temp2[i], ss);
+      ss = warp_sum(ss);
+      if (lane == 0) S.ss = ss;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      if (j > 1) Hat(j - 1, j - 2) = S.true_nrm;
+      double t = temp2[j];
+      double awn = sqrt(t);
+      S.scale = 1.0;
+      if (t < S.ss) {                         // Pythagorean radicand negative: explicit norm
+        ctl->fallbacks += 1;
+        ctl->fallback_pending = 1;
+        ctl->nrm_est = 1.0;
+      } else {
+        double ne = sqrt(t - S.ss);           // Eq. 18
+        if (!(ne > P.brk_tol * awn)) {
+          Hat(j, j - 1) = ne;
+          ctl->m_eff = j;
+          ctl->breakdown = 1;
+          ctl->done = 1;
+        }
+        ctl->nrm_est = ne;
+        S.scale = (ne > 0.0) ? 1.0 / ne : 0.0;
+      }
+      ctl->aw_prev = awn;
+      ctl->a = S.sj * S.scale;
+      if (j == P.m && !ctl->done) ctl->m_eff = P.m;
+    }
+    __syncthreads();
+    for (int i = tid; i < j; i += NT) {
+      double si = (i == j - 1) ? S.sj : __ldcg(&ctl->sigma[i]);
+      ctl->coef[i] = si * hcol[i] * S.scale;
+    }
+  }
+
+  // small[r][k] = M[r][k] for r < rows, k < r (strictly lower part), from global.
+  __device__ void stage(const double* M, int rows) {
+    for (int e = tid; e < rows * MMAX; e += NT) {
+      int r = e / MMAX, k = e - r * MMAX;
+      if (k < r) S.small[e] = __ldcg(M + e);
+    }
+    __syncthreads();
+  }
+
+  // out[r] = in[r] + sum_{k<r} small[r][k] in[k]  (unit lower-triangular times vector), r < n
+  __device__ void apply_unit_lower(const double* in, double* out, int n) {
+    for (int r = warp; r < n; r += NW) {
+      double acc = 0.0;
+      for (int k = lane; k < r; k += 32) acc = fma(S.small[r * MMAX + k], in[k], acc);
+      acc = warp_sum(acc);
+      if (lane == 0) out[r] = in[r] + acc;
+    }
+    __syncthreads();
+  }
+
+  __device__ void hybrid_fallback_finish(int j) {
+    Ctl* ctl = P.ctl;
+    if (tid == 0) {
+      double nrm = sqrt(S.red[0]);
+      ctl->syncs += 1;
+      if (!(nrm > P.brk_tol * ctl->aw_prev)) {
+        Hat(j, j - 1) = nrm;
+        ctl->m_eff = j;
+        ctl->breakdown = 1;
+        ctl->done = 1;
+      }
+      ctl->nrm_est = nrm;
+      S.scale = (nrm > 0.0) ? 1.0 / nrm : 0.0;
+      ctl->a = __ldcg(&ctl->a) * S.scale;
+      ctl->fallback_pending = 0;
+    }
+    __syncthreads();
+    for (int i = tid; i < j; i += NT) ctl->coef[i] = __ldcg(&ctl->coef[i]) * S.scale;
+  }
+
+  __device__ void hybrid_final_finish() {
+    Ctl* ctl = P.ctl;
+    if (tid == 0) {
+      const int m = P.m;
+      double nrm = sqrt(S.red[0]);
+      double hl = ctl->nrm_est * nrm;       // true norm of the projected v_{m+1}
+      Hat(m, m - 1) = hl;
+      ctl->h_last = hl;
+      ctl->sigma[m] = (nrm > 0.0) ? 1.0 / nrm : 0.0;
+      ctl->syncs += 1;
+      if (!(hl > P.brk_tol * ctl->aw_prev)) ctl->breakdown = 1;
+    }
+  }
+
+  // -------------------------------------------------------------------------
+  // Hybrid low-synchronisation Arnoldi (Alg. 4).  Storage: column j-1 holds
+  // x_j = u_j / nrm_est_{j-1} (u_j the projected vector); the normalised
+  // v_j = sigma_j x_j with sigma_j = 1/||x_j|| known after step j.  All the
+  // rescalings of Alg. 4 are folded into the scalars a, coef and sigma.
+  __device__ void run_hybrid() {
+    B* V = reinterpret_cast<B*>(P.V);
+    B* Wb[2] = {reinterpret_cast<B*>(P.W0), reinterpret_cast<B*>(P.W1)};
+    const long long N = P.op.N;
+    const int m = P.m;
+    unsigned gen = 0;
+    if (tid == 0) { S.a = (Tc)1; S.done = 0; S.fallback_pending = 0; }
+    __syncthreads();
+    for (int j = 1; j <= m; ++j) {
+      PassT<B> ps;
+      ps.c0 = 0; ps.c1 = j - 1;
+      ps.a = (j == 1) ? 1.0 : (double)S.a;
+      ps.src64 = (j == 1) ? P.vin : nullptr;
+      ps.srcB = (j == 1) ? nullptr : Wb[(j - 1) & 1];
+      ps.xout = V + (long long)(j - 1) * N;
+      ps.wout = Wb[j & 1];
+      ps.d0 = 0; ps.d1 = j - 1;
+      ps.dmode = DOT_X | DOT_W;
+      ps.self = SELF_XX | SELF_XW | SELF_WW;
+      int ns = run_pass(ps);
+      if (!reduce_step(gen, ns, j, [&] { hybrid_step(j); })) return;
+      if (S.done) return;
+      if (S.fallback_pending) {
+        // explicit norm of the projected vector (extra reduction of Alg. 4)
+        PassT<B> pf;
+        pf.c0 = 0; pf.c1 = j; pf.a = (double)S.a;
+        pf.src64 = nullptr; pf.srcB = Wb[j & 1];
+        pf.xout = nullptr; pf.wout = nullptr;
+        pf.d0 = 0; pf.d1 = 0; pf.dmode = 0; pf.self = SELF_XX;
+        int nf = run_pass(pf);
+        if (!reduce_step(gen, nf, j, [&] { hybrid_fallback_finish(j); })) return;
+        if (S.done) return;
+      }
+    }
+    // final projection of v_{m+1} and its norm (one more reduction)
+    PassT<B> pl;
+    pl.c0 = 0; pl.c1 = m; pl.a = (double)S.a;
+    pl.src64 = nullptr; pl.srcB = Wb[m & 1];
+    pl.xout = V + (long long)m * N; pl.wout = nullptr;
+    pl.d0 = 0; pl.d1 = 0; pl.dmode = 0; pl.self = SELF_XX;
+    int nl = run_pass(pl);
+    reduce_step(gen, nl, 0, [&] { hybrid_final_finish(); });
+  }
+
+  // -------------------------------------------------------------------------
+  // Shared pieces of MGS and CGS2: ||v|| and the "next vector" pass.
+  __device__ bool norm_of_input(unsigned& gen) {
+    PassT<B> ps;
+    ps.c0 = ps.c1 = 0; ps.a = 1.0; ps.src64 = P.vin; ps.srcB = nullptr;
+    ps.xout = nullptr; ps.wout = nullptr; ps.d0 = ps.d1 = 0; ps.dmode = 0; ps.self = SELF_XX;
+    int ns = run_pass(ps);
+    return reduce_step(gen, ns, 0, [&] {
+      if (tid == 0) {
+        double b = sqrt(S.red[0]);
+        P.ctl->beta = b;
+        P.ctl->syncs += 1;
+        if (b == 0.0) { P.ctl->done = 1; P.ctl->m_eff = 0; }     // zero start vector: y = 0
+        else if (!isfinite(b)) { P.ctl->done = 1; P.ctl->status = (int)LSA_ERR_NUMERIC; }
+        P.ctl->a = (b > 0.0) ? 1.0 / b : 0.0;
+        for (int i = 0; i <= P.m; ++i) P.ctl->sigma[i] = 1.0;
+      }
+    });
+  }
+
+  // write v_{m+1} = a * w (no reduction): only for the Arnoldi output
+  __device__ void write_last(B* dst, const B* src) {
+    PassT<B> ps;
+    ps.c0 = ps.c1 = 0; ps.a = (double)S.a; ps.src64 = nullptr; ps.srcB = src;
+    ps.xout = dst; ps.wout = nullptr; ps.d0 = ps.d1 = 0; ps.dmode = 0; ps.self = 0;
+    run_pass(ps);
+  }
+
+  // Alg. 1: Arnoldi with modified Gram-Schmidt (j+1 reductions at step j).
+  __device__ void run_mgs(bool write_vlast) {
+    B* V = reinterpret_cast<B*>(P.V);
+    B* Wb[2] = {reinterpret_cast<B*>(P.W0), reinterpret_cast<B*>(P.W1)};
+    const long long N = P.op.N;
+    const int m = P.m;
+    unsigned gen = 0;
+    if (!norm_of_input(gen)) return;
+    if (S.done) return;
+    for (int j = 1; j <= m; ++j) {
+      B* w = Wb[j & 1];
+      // v_j = a * (previous w or b); w = A v_j; v_1 . w; ||w||^2
+      PassT<B> pa;
+      pa.c0 = pa.c1 = 0; pa.a = (double)S.a;
+      pa.src64 = (j == 1) ? P.vin : nullptr;
+      pa.srcB = (j == 1) ? nullptr : Wb[(j - 1) & 1];
+      pa.xout = V + (long long)(j - 1) * N; pa.wout = w;
+      pa.d0 = 0; pa.d1 = (j > 1) ? 1 : 0; pa.dmode = DOT_W;
+      pa.self = SELF_XW | SELF_WW;
+      int ns = run_pass(pa);
+      if (!reduce_step(gen, ns, 1, [&] {
+            if (tid == 0) {
+              const int nd = (j > 1) ? 1 : 0;
+              // H_{1,j} = v_1 . w: the W slot of column 0, or x.w when v_1 = x
+              double h = (j > 1) ? S.red[nd] : S.red[2 * nd + 1];
+              Hat(0, j - 1) = h;
+              P.ctl->coef[0] = h;
+              P.ctl->aw_prev = sqrt(S.red[2 * nd + 2]);
+              P.ctl->syncs += 1;
+            }
+          })) return;
+      for (int i = 1; i < j; ++i) {
+        // w -= H_{i,j} v_i ; v_{i+1} . w
+        PassT<B> pu;
+        pu.c0 = i - 1; pu.c1 = i; pu.a = 1.0; pu.src64 = nullptr; pu.srcB = w;
+        pu.xout = w; pu.wout = nullptr;
+        pu.d0 = i; pu.d1 = i + 1; pu.dmode = DOT_X; pu.self = 0;
+        int nu = run_pass(pu);
+        if (!reduce_step(gen, nu, i + 1, [&] {
+              if (tid == 0) {
+                double h = S.red[0];
+                Hat(i, j - 1) = h;
+                P.ctl->coef[i] = h;
+                P.ctl->syncs += 1;
+              }
+            })) return;
+      }
+      // w -= H_{j,j} v_j ; ||w||
+      PassT<B> pz;
+      pz.c0 = j - 1; pz.c1 = j; pz.a = 1.0; pz.src64 = nullptr; pz.srcB = w;
+      pz.xout = w; pz.wout = nullptr; pz.d0 = pz.d1 = 0; pz.dmode = 0; pz.self = SELF_XX;
+      int nz = run_pass(pz);
+      if (!reduce_step(gen, nz, 0, [&] { finish_norm(j); })) return;
+      if (S.done) return;
+    }
+    if (write_vlast) write_last(V + (long long)m * N, Wb[m & 1]);
+  }
+
+  __device__ void finish_norm(int j) {
+    if (tid == 0) {
+      Ctl* ctl = P.ctl;
+      double nrm = sqrt(S.red[0]);
+      Hat(j, j - 1) = nrm;
+      ctl->syncs += 1;
+      if (!(nrm > P.brk_tol * ctl->aw_prev)) {
+        ctl->m_eff = j;
+        ctl->breakdown = 1;
+        ctl->done = 1;
+      }
+      if (!isfinite(nrm)) { ctl->status = (int)LSA_ERR_NUMERIC; ctl->done = 1; ctl->m_eff = j - 1; }
+      ctl->a = (nrm > 0.0) ? 1.0 / nrm : 0.0;
+      ctl->h_last = nrm;
+      if (j == P.m && !ctl->done) ctl->m_eff = P.m;
+    }
+  }
+
+  // Classical Gram-Schmidt twice (3 reductions per step).
+  __device__ void run_cgs2(bool write_vlast) {
+    B* V = reinterpret_cast<B*>(P.V);
+    B* Wb[2] = {reinterpret_cast<B*>(P.W0), reinterpret_cast<B*>(P.W1)};
+    const long long N = P.op.N;
+    const int m = P.m;
+    unsigned gen = 0;
+    if (!norm_of_input(gen)) return;
+    if (S.done) return;
+    for (int j = 1; j <= m; ++j) {
+      B* w = Wb[j & 1];
+      PassT<B> pa;
+      pa.c0 = pa.c1 = 0; pa.a = (double)S.a;
+      pa.src64 = (j == 1) ? P.vin : nullptr;
+      pa.srcB = (j == 1) ? nullptr : Wb[(j - 1) & 1];
+      pa.xout = V + (long long)(j - 1) * N; pa.wout = w;
+      pa.d0 = 0; pa.d1 = j - 1; pa.dmode = DOT_W;
+      pa.self = SELF_XW | SELF_WW;
+      int ns = run_pass(pa);
+      if (!reduce_step(gen, ns, j, [&] {
+            const int nd = j - 1;
+            for (int i = tid; i < j; i += NT) {
+              double h = (i < nd) ? S.red[nd + i] : S.red[2 * nd + 1];
+              P.ctl->hcol[i] = h;
+              P.ctl->coef[i] = h;
+            }
+            if (tid == 0) { P.ctl->aw_prev = sqrt(S.red[2 * nd + 2]); P.ctl->syncs += 1; }
+          })) return;
+      PassT<B> pb;
+      pb.c0 = 0; pb.c1 = j; pb.a = 1.0; pb.src64 = nullptr; pb.srcB = w;
+      pb.xout = w; pb.wout = nullptr; pb.d0 = 0; pb.d1 = j; pb.dmode = DOT_X; pb.self = 0;
+      int nb = run_pass(pb);
+      if (!reduce_step(gen, nb, j, [&] {
+            for (int i = tid; i < j; i += NT) {
+              double h2 = S.red[i];
+              Hat(i, j - 1) = __ldcg(&P.ctl->hcol[i]) + h2;
+              P.ctl->coef[i] = h2;
+            }
+            if (tid == 0) P.ctl->syncs += 1;
+          })) return;
+      PassT<B> pc;
+      pc.c0 = 0; pc.c1 = j; pc.a = 1.0; pc.src64 = nullptr; pc.srcB = w;
+      pc.xout = w; pc.wout = nullptr; pc.d0 = pc.d1 = 0; pc.dmode = 0; pc.self = SELF_XX;
+      int nc = run_pass(pc);
+      if (!reduce_step(gen, nc, 0, [&] { finish_norm(j); })) return;
+      if (S.done) return;
+    }
+    if (write_vlast) write_last(V + (long long)m * N, Wb[m & 1]);
+  }
+};
+
+template <class Op, class Tc, class B>
+__global__ void __launch_bounds__(NT, 2) k_arnoldi(ArnoldiParams P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  using E = Engine<Op, Tc, B>;
+  typename E::Smem& S = *reinterpret_cast<typename E::Smem*>(smem_raw);
+  E e(P, S);
+  if (P.variant == LSA_MGS) e.run_mgs(P.write_vlast != 0);
+  else if (P.variant == LSA_CGS2) e.run_cgs2(P.write_vlast != 0);
+  else e.run_hybrid();
+}
+
+// One stencil pass y = A x with the same tile code (no barrier).
+template <class Op, class Tc, class B>
+__global__ void __launch_bounds__(NT) k_matvec(ArnoldiParams P, const B* x, B* y) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  using E = Engine<Op, Tc, B>;
+  typename E::Smem& S = *reinterpret_cast<typename E::Smem*>(smem_raw);
+  E e(P, S);
+  if (threadIdx.x == 0) S.a = (Tc)1;
+  __syncthreads();
+  PassT<B> ps;
+  ps.c0 = ps.c1 = 0; ps.a = 1.0; ps.src64 = nullptr; ps.srcB = x;
+  ps.xout = nullptr; ps.wout = y; ps.d0 = ps.d1 = 0; ps.dmode = 0; ps.self = 0;
+  e.run_pass(ps);
+}
+
+template <class Op>
+cudaError_t launch_arnoldi_op(const ArnoldiParams& P, int precision, int G, cudaStream_t s) {
+  ArnoldiParams Pc = P;
+  void* args[1] = {&Pc};
+  if (precision == LSA_FP64) {
+    auto k = k_arnoldi<Op, double, double>;
+    size_t sm = sizeof(typename Engine<Op, double, double>::Smem);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchCooperativeKernel((void*)k, dim3(G), dim3(NT), args, sm, s);
+  } else {
+    auto k = k_arnoldi<Op, float, float>;
+    size_t sm = sizeof(typename Engine<Op, float, float>::Smem);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchCooperativeKernel((void*)k, dim3(G), dim3(NT), args, sm, s);
+  }
+}
+
+template <class Op>
+cudaError_t launch_matvec_op(const ArnoldiParams& P, int precision, const void* x, void* y, int G,
+                             cudaStream_t s) {
+  if (precision == LSA_FP64) {
+    auto k = k_matvec<Op, double, double>;
+    size_t sm = sizeof(typename Engine<Op, double, double>::Smem);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k<<<G, NT, sm, s>>>(P, (const double*)x, (double*)y);
+  } else {
+    auto k = k_matvec<Op, float, float>;
+    size_t sm = sizeof(typename Engine<Op, float, float>::Smem);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k<<<G, NT, sm, s>>>(P, (const float*)x, (float*)y);
+  }
+  return cudaGetLastError();
+}
+
+template <class Op>
+int blocks_per_sm_op(int precision) {
+  int nb = 0;
+  if (precision == LSA_FP64) {
+    auto k = k_arnoldi<Op, double, double>;
+    size_t sm = sizeof(typename Engine<Op, double, double>::Smem);
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, NT, sm);
+  } else {
+    auto k = k_arnoldi<Op, float, float>;
+    size_t sm = sizeof(typename Engine<Op, float, float>::Smem);
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, NT, sm);
+  }
+  return nb;
+}
+
+}  // namespace lsa

@@ -1,0 +1,220 @@
+// Internal declarations shared by the CUDA translation units of liblsarnoldi.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/lsarnoldi.h"
+
+namespace lsa {
+
+constexpr int MMAX = 64;                  // largest Krylov dimension of the fused kernels
+constexpr int PMAX = 8;                   // largest phi index p
+constexpr int SLOTS = 2 * MMAX + 4;       // reduction slots per CTA and pass
+constexpr int NT = 256;                   // threads per CTA of the Arnoldi kernels
+constexpr int NW = NT / 32;
+constexpr int TX = 16, TY = 16;           // tile footprint (grid points) in x and y
+constexpr int PW = TX + 2, PH = TY + 2;   // footprint plus a one-point halo
+constexpr int PS = PW * PH;               // plane size in shared memory
+constexpr int KMAX = (MMAX + NW - 1) / NW; // basis columns per warp in the dot phase
+constexpr int NMAX_SMALL = MMAX + PMAX + 1; // largest augmented Hessenberg size
+constexpr int SMALL_STRIDE = NMAX_SMALL;    // leading dimension of small dense matrices
+
+// Device-side control block, one per workspace.  Written only by the CTA that
+// arrives last at a grid barrier (between barriers), read by all after it.
+struct Ctl {
+  unsigned int arrive;     // grid-barrier arrivals (monotonic within a launch)
+  unsigned int release;    // last released barrier generation
+  unsigned int e_arrive;   // barrier of the small-exponential kernel
+  unsigned int e_release;
+  int status;              // device-side lsa_status
+  int abort_flag;          // set on a barrier timeout: every CTA leaves
+  int m_eff;
+  int breakdown;
+  int fallbacks;
+  int syncs;               // reductions performed
+  int barriers;            // grid barriers performed (with or without reduction)
+  int done;                // the Arnoldi loop has ended (breakdown)
+  int fallback_pending;    // next pass is the explicit-norm fallback pass (Alg. 4)
+  int expm_s;              // squarings used by the small exponential
+  double beta;
+  double nrm_est;          // current norm estimate (hybrid)
+  double a;                // scale of the source vector in the next projection
+  double aw_prev;          // ||A v_j|| of the last completed step (normalised units)
+  double h_last;           // H_{m+1,m}
+  double err_est;
+  double red[SLOTS];       // reduced sums of the last reduction
+  double coef[MMAX + 2];   // projection coefficients of the next pass
+  double sigma[MMAX + 2];  // lazy scales of the stored basis columns
+  double hcol[MMAX + 2];
+};
+
+// Operator as the kernels see it: geometry, folded stencil coefficients, fields.
+struct DevOp {
+  int kind;
+  int nx, ny, nz;
+  int ns;                  // species (2 for Gray-Scott)
+  long long npts;          // nx*ny*nz
+  long long N;             // ns*npts
+  // advdiff2d / adr3d: folded neighbour coefficients; center excludes r
+  double cW, cE, cS, cN, cD, cU, cC;
+  // grayscott2d
+  double du, dv, F, k;     // du = Du/dx^2, dv = Dv/dx^2
+  const double* f0;        // fp64 fields (u0 / r)
+  const double* f1;        // fp64 field v0
+  const float* g0;         // fp32 fields for the FP32-basis form (a=v0^2 / r)
+  const float* g1;         // fp32 field b=2 u0 v0
+};
+
+struct Tiling {
+  int tiles_x, tiles_y, zsegs, ZS;
+  int ntiles;
+};
+
+struct ArnoldiParams {
+  DevOp op;
+  Tiling tl;
+  const double* vin;       // start vector (fp64)
+  void* V;                 // basis, N x (m+1)
+  void* W0;                // matvec ping-pong buffers
+  void* W1;
+  double* H;               // (m+1) x m column-major, leading dimension m+1
+  Ctl* ctl;
+  double* partials;        // gridDim.x x SLOTS
+  double* T;               // MMAX x MMAX correction matrix (CWY/NCWY T, GSMGS M^{-1})
+  double* L;               // MMAX x MMAX strictly lower part of V^T V (GSMGS)
+  int m;
+  int variant;
+  int write_vlast;         // MGS/CGS2: write v_{m+1} (Arnoldi output only)
+  double brk_tol;
+  long long timeout_ns;
+};
+
+// Workspace layout (all offsets 256-byte aligned).
+struct Layout {
+  size_t ctl, partials, T, L, H, V, W0, W1, small, coefs, g0, g1, total;
+  int G;                   // CTAs of the persistent Arnoldi kernel
+};
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Host helpers implemented in lsa_api.cu
+bool make_devop(const lsa_op* op, DevOp* d);
+Tiling make_tiling(const DevOp& d);
+
+// Launchers implemented per operator translation unit.
+cudaError_t launch_arnoldi(const ArnoldiParams& P, int precision, int G, cudaStream_t s);
+cudaError_t launch_matvec(const ArnoldiParams& P, int precision, const void* x, void* y, int G,
+                          cudaStream_t s);
+int arnoldi_blocks_per_sm(const DevOp& d, int precision);
+
+// Small kernels (lsa_small.cu)
+struct SmallParams {
+  const double* H;         // Hessenberg source, column-major, leading dimension ldh
+  int ldh;
+  const Ctl* ctl_in;       // when non-null, m_eff / beta / sigma / h_last come from here
+  Ctl* ctl;                // expm status/err_est output (may equal ctl_in)
+  int m;                   // used when ctl_in is null
+  int p;
+  double h;
+  double* mats;            // 6 scratch matrices of SMALL_STRIDE^2 doubles
+  double* C;               // output coefficients: (p+2) x ldc, row k = phi_k(hH)e_1 (scaled)
+  int ldc;
+  int scale_out;           // 1: fold beta * sigma_i into rows 0..p (for the combine kernel)
+  long long timeout_ns;
+  double tol;
+};
+cudaError_t launch_expm(const SmallParams& P, cudaStream_t s);
+cudaError_t launch_combine(const void* V, int precision, long long N, const double* C, int ldc,
+                           int p, const Ctl* ctl, double* y, cudaStream_t s);
+cudaError_t launch_init(Ctl* ctl, const DevOp& op, float* g0, float* g1, int precision,
+                        double* H, int ldh_total, cudaStream_t s);
+cudaError_t launch_scale_basis(void* V, int precision, long long N, int m, const Ctl* ctl,
+                               cudaStream_t s);
+cudaError_t launch_timeout_selftest(Ctl* ctl, long long timeout_ns, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Device helpers
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ int ld_volatile_i32(const int* p) {
+  return *(volatile const int*)p;
+}
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Grid barrier with a bounded wait.  All `count` participating CTAs call it
+// with the same generation number `gen` (0, 1, 2, ...).  Returns 1 in the CTA
+// that arrived last (which must later call barrier_release), 0 in the others
+// once released, -1 on timeout or abort (the caller must leave the kernel).
+// Must be called by all threads of the CTA; `s_flag` is a shared int.
+struct BarrierRef {
+  unsigned* arrive;
+  unsigned* release;
+  int* abort_flag;
+  int* status;
+};
+
+__device__ __forceinline__ int barrier_arrive(const BarrierRef& b, unsigned gen, unsigned count,
+                                              int* s_flag, long long timeout_ns) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned old = atomicAdd(b.arrive, 1u);
+    int last = (old == (gen + 1u) * count - 1u);
+    int res = last ? 1 : 0;
+    if (!last) {
+      unsigned long long t0 = global_ns();
+      unsigned it = 0;
+      while (ld_acquire_u32(b.release) < gen + 1u) {
+        if ((++it & 255u) == 0u) {
+          if (ld_volatile_i32(b.abort_flag)) { res = -1; break; }
+          if ((long long)(global_ns() - t0) > timeout_ns) {
+            atomicExch(b.abort_flag, 1);
+            atomicCAS(b.status, 0, (int)LSA_ERR_TIMEOUT);
+            res = -1;
+            break;
+          }
+          if (it > 4096u) __nanosleep(64);
+        }
+      }
+    }
+    *s_flag = res;
+  }
+  __syncthreads();
+  int r = *s_flag;
+  if (r == 1) __threadfence();
+  return r;
+}
+
+__device__ __forceinline__ void barrier_release(const BarrierRef& b, unsigned gen) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) st_release_u32(b.release, gen + 1u);
+}
+
+__device__ __forceinline__ BarrierRef arnoldi_barrier(Ctl* c) {
+  return BarrierRef{&c->arrive, &c->release, &c->abort_flag, &c->status};
+}
+__device__ __forceinline__ BarrierRef expm_barrier(Ctl* c) {
+  return BarrierRef{&c->e_arrive, &c->e_release, &c->abort_flag, &c->status};
+}
+
+}  // namespace lsa
