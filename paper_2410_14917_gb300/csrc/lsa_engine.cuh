@@ -189,54 +189,60 @@ struct Engine {
   }
 
   // Inner products of basis columns [d0, d1) with the plane's x and/or w:
-  // warp <-> columns, lane <-> interior points.
+  // warp <-> columns, lane <-> interior points (species one after the other,
+  // to bound the registers that hold the point values).
   __device__ void dots_plane(const PassT<B>& ps, int x0, int y0, int z, int w, int hg, int sl) {
     if (ps.d1 <= ps.d0) return;
+    constexpr int NPS = (TX * TY + 31) / 32;   // points per lane and species
     const DevOp& d = P.op;
     const int pint = w * hg;
-    const int count = NS * pint;
-    const Tc* xr = S.ring + sl * NS * PS;
-    Tc xv[NPL], wv[NPL];
-    int gi[NPL];
-#pragma unroll
-    for (int k = 0; k < NPL; ++k) {
-      int ql = lane + 32 * k;
-      if (ql < count) {
-        int s = ql / pint, q = ql - s * pint;
-        int ly = q / w, lx = q - ly * w;
-        xv[k] = xr[s * PS + (ly + 1) * PW + lx + 1];
-        wv[k] = (ps.dmode & DOT_W) ? S.wbuf[s * TX * TY + q] : (Tc)0;
-        gi[k] = (int)(s * d.npts + (x0 + lx) + (long long)d.nx * ((y0 + ly) + (long long)d.ny * z));
-      } else {
-        xv[k] = 0; wv[k] = 0; gi[k] = 0;
-      }
-    }
     const bool dx = ps.dmode & DOT_X, dw = ps.dmode & DOT_W;
+#pragma unroll 1
+    for (int s = 0; s < NS; ++s) {
+      const Tc* xr = S.ring + sl * NS * PS + s * PS;
+      Tc xv[NPS], wv[NPS];
+      int gi[NPS];
 #pragma unroll
-    for (int kk = 0; kk < KMAX; ++kk) {
-      int c = ps.d0 + warp + NW * kk;
-      if (c < ps.d1) {
-        const B* base = Vc(c);
-        if constexpr (F64) {
-          double px = 0, pw = 0;
-#pragma unroll
-          for (int k = 0; k < NPL; ++k) {
-            double v = (double)__ldcg(base + gi[k]);
-            px = fma(v, (double)xv[k], px);
-            pw = fma(v, (double)wv[k], pw);
-          }
-          if (dx) ax[kk] += px;
-          if (dw) aw[kk] += pw;
+      for (int k = 0; k < NPS; ++k) {
+        int q = lane + 32 * k;
+        if (q < pint) {
+          int ly = q / w, lx = q - ly * w;
+          xv[k] = xr[(ly + 1) * PW + lx + 1];
+          wv[k] = dw ? S.wbuf[s * TX * TY + q] : (Tc)0;
+          gi[k] = (int)(s * d.npts + (x0 + lx) + (long long)d.nx * ((y0 + ly) + (long long)d.ny * z));
         } else {
-          float px = 0.f, pw = 0.f;
+          xv[k] = 0; wv[k] = 0; gi[k] = 0;
+        }
+      }
 #pragma unroll
-          for (int k = 0; k < NPL; ++k) {
-            float v = (float)__ldcg(base + gi[k]);
-            px = fmaf(v, (float)xv[k], px);
-            pw = fmaf(v, (float)wv[k], pw);
+      for (int kk = 0; kk < KMAX; ++kk) {
+        int c = ps.d0 + warp + NW * kk;
+        if (c < ps.d1) {
+          const B* base = Vc(c);
+          if constexpr (F64) {
+            double px0 = 0, pw0 = 0, px1 = 0, pw1 = 0;   // two chains each: more FP64 ILP
+#pragma unroll
+            for (int k = 0; k < NPS; k += 2) {
+              double v0 = (double)__ldcg(base + gi[k]);
+              double v1 = (double)__ldcg(base + gi[k + 1]);
+              px0 = fma(v0, (double)xv[k], px0);
+              pw0 = fma(v0, (double)wv[k], pw0);
+              px1 = fma(v1, (double)xv[k + 1], px1);
+              pw1 = fma(v1, (double)wv[k + 1], pw1);
+            }
+            if (dx) ax[kk] += px0 + px1;
+            if (dw) aw[kk] += pw0 + pw1;
+          } else {
+            float px = 0.f, pw = 0.f;
+#pragma unroll
+            for (int k = 0; k < NPS; ++k) {
+              float v = (float)__ldcg(base + gi[k]);
+              px = fmaf(v, (float)xv[k], px);
+              pw = fmaf(v, (float)wv[k], pw);
+            }
+            if (dx) kahan(axs[kk], axc[kk], px);
+            if (dw) kahan(aws[kk], awc[kk], pw);
           }
-          if (dx) kahan(axs[kk], axc[kk], px);
-          if (dw) kahan(aws[kk], awc[kk], pw);
         }
       }
     }
@@ -308,20 +314,25 @@ struct Engine {
     return 2 * nd + 3;
   }
 
-  // Last CTA: fixed-order reduction of all CTAs' partials into S.red.
+  // Last CTA: fixed-order reduction of all CTAs' partials into S.red.  Warp w
+  // takes slots w, w+NW, ...; lane l sums CTAs l, l+32, ... in order (all its
+  // loads are independent, so they are in flight together), then a fixed
+  // butterfly combines the lanes: the result is deterministic for a given grid.
   __device__ void reduce_partials(int nslots) {
     const int G = gridDim.x;
-    for (int s = tid; s < nslots; s += NT) {
-      double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-      int c = 0;
-      for (; c + 4 <= G; c += 4) {
-        a0 += __ldcg(P.partials + (long long)c * SLOTS + s);
-        a1 += __ldcg(P.partials + (long long)(c + 1) * SLOTS + s);
-        a2 += __ldcg(P.partials + (long long)(c + 2) * SLOTS + s);
-        a3 += __ldcg(P.partials + (long long)(c + 3) * SLOTS + s);
+    for (int s = warp; s < nslots; s += NW) {
+      const double* ps = P.partials + s;
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      int c = lane;
+      for (; c + 96 < G; c += 128) {
+        a0 += __ldcg(ps + (long long)c * SLOTS);
+        a1 += __ldcg(ps + (long long)(c + 32) * SLOTS);
+        a2 += __ldcg(ps + (long long)(c + 64) * SLOTS);
+        a3 += __ldcg(ps + (long long)(c + 96) * SLOTS);
       }
-      for (; c < G; ++c) a0 += __ldcg(P.partials + (long long)c * SLOTS + s);
-      S.red[s] = (a0 + a1) + (a2 + a3);
+      for (; c < G; c += 32) a0 += __ldcg(ps + (long long)c * SLOTS);
+      double v = warp_sum((a0 + a1) + (a2 + a3));
+      if (lane == 0) S.red[s] = v;
     }
     __syncthreads();
   }
