@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-flush", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle leg (profiling runs)")
+    ap.add_argument("--size", type=int, default=0, help="override the grid side (profiling on a smaller case)")
     return ap.parse_args()
 
 
@@ -71,12 +72,15 @@ def load_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def workload(cfg_index):
+def workload(cfg_index, size=0):
     import workloads as W
 
     cfg = W.config(cfg_index)
     if cfg.get("kind") == "batched":
         raise SystemExit("the batched workload is a parity case, not a bench line")
+    if size:
+        ctor = {"advdiff2d": W.advdiff2d, "grayscott2d": W.grayscott2d, "adr3d": W.adr3d}[cfg["kind"]]
+        cfg = ctor(size, h=cfg["h"], p=cfg["p"], m=cfg["m"], seed=cfg["seed"])
     return cfg
 
 
@@ -164,7 +168,7 @@ def run_reference(args, world, rank):
     from oracle import krylov as OK
     from oracle import operators as OP
 
-    cfg = workload(args.config)
+    cfg = workload(args.config, args.size)
     inp = W.make_inputs(cfg)
     A = OP.from_workload(cfg, inp)
     variant = args.variant
@@ -233,7 +237,7 @@ def main():
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    cfg = workload(args.config)
+    cfg = workload(args.config, args.size)
     inp = W.make_inputs(cfg)
     N = W.n_dof(cfg)
     p, m, h = cfg["p"], cfg["m"], cfg["h"]
