@@ -153,6 +153,30 @@ lsa_status lsa_phiv(const lsa_op* op, const double* v, double h, int p, int m, d
 lsa_status lsa_expm_phi(const double* H, int ldh, int m, double h, int p, double* C,
                         void* work, size_t work_bytes, void* stream);
 
+/* Size of the fixed device workspace used by lsa_phiv_noalloc (32 MiB). */
+#define LSA_STATIC_WORKSPACE_BYTES (32u << 20)
+
+/* lsa_phiv for callers that cannot allocate device memory -- plugins inside a
+ * host application that owns the device memory through its own pool, and
+ * latency-critical code that must not call cudaMalloc/cudaFree after start-up
+ * (they can synchronise the device).  The paper has no counterpart: this is a
+ * deployment convenience of this library.
+ *  Arguments and results as lsa_phiv, without work/work_bytes: the workspace
+ *  is a static device array of LSA_STATIC_WORKSPACE_BYTES inside the library,
+ *  held by every GPU that loads the library until the process exits.
+ *  Returns LSA_ERR_WORKSPACE when lsa_workspace_bytes(op, min(m, N), p,
+ *  precision) exceeds that size (nothing is launched then).
+ *  The first call on a device looks up the array's device address
+ *  (cudaGetSymbolAddress, with that device current); make that first call
+ *  before any stream capture.  All calls share the one array and it keeps the
+ *  last call's contents (each call re-initialises what must start at zero), so
+ *  calls whose work overlaps on the GPU -- on different streams, or from
+ *  different host threads -- race and must be serialised by the caller.
+ *  The call allocates nothing (no cudaMalloc/cudaFree, no event creation). */
+lsa_status lsa_phiv_noalloc(const lsa_op* op, const double* v, double h, int p, int m, double tol,
+                            int variant, int precision, double* y, lsa_stats* stats,
+                            void* stream);
+
 /* Synchronise `stream` and read the statistics of the last call that used `work`. */
 lsa_status lsa_read_stats(const void* work, lsa_stats* out, void* stream);
 

@@ -19,7 +19,7 @@ import torch
 from . import _binding as B
 from ._binding import LsaError, LsaOp, LsaStats, PRECISIONS, VARIANTS, KINDS
 
-__all__ = ["Operator", "phiv", "arnoldi", "matvec", "expm_phi", "workspace_bytes", "read_stats",
+__all__ = ["Operator", "phiv", "phiv_noalloc", "arnoldi", "matvec", "expm_phi", "workspace_bytes", "read_stats",
            "selftest_barrier_timeout", "max_m", "LsaError", "Workspace"]
 
 
@@ -160,6 +160,22 @@ def phiv(op: Operator, v: torch.Tensor, h: float, p: int, m: int, tol: float = 0
                           ctypes.c_void_p(work.ptr), work.nbytes,
                           ctypes.byref(s) if stats else None, _stream_ptr(stream))
     _check(st, "lsa_phiv")
+    return y, (s.as_dict() if stats else None)
+
+
+def phiv_noalloc(op: Operator, v: torch.Tensor, h: float, p: int, m: int, tol: float = 0.0,
+                 variant="hcwy", precision="fp64", y=None, stream=None, stats=True):
+    """phiv through lsa_phiv_noalloc: the library's fixed static device workspace
+    is used instead of a caller-provided one (for callers that cannot allocate)."""
+    if v.dtype != torch.float64 or not v.is_cuda or not v.is_contiguous():
+        raise ValueError("v must be a contiguous float64 CUDA tensor")
+    N = v.numel()
+    y = torch.empty((p + 1, N), dtype=torch.float64, device=v.device) if y is None else y
+    s = LsaStats()
+    st = B.lib().lsa_phiv_noalloc(ctypes.byref(op.c), _ptr(v), float(h), int(p), int(m), float(tol),
+                                  VARIANTS[variant], PRECISIONS[precision], _ptr(y),
+                                  ctypes.byref(s) if stats else None, _stream_ptr(stream))
+    _check(st, "lsa_phiv_noalloc")
     return y, (s.as_dict() if stats else None)
 
 
