@@ -63,7 +63,8 @@ struct Engine {
   // dot accumulators (per lane)
   double ax[KMAX], aw[KMAX];
   float axs[KMAX], axc[KMAX], aws[KMAX], awc[KMAX];
-  double sxx, sxw, sww;
+  double sxx, sxw, sww;              // self terms (float64 form)
+  float fxx[2], fxw[2], fww[2];      // self terms (float32 form): Kahan sum, compensation
 
   __device__ Engine(const ArnoldiParams& p, Smem& s)
       : P(p), S(s), tid(threadIdx.x), lane(threadIdx.x & 31), warp(threadIdx.x >> 5) {
@@ -78,6 +79,21 @@ struct Engine {
 #pragma unroll
     for (int k = 0; k < KMAX; ++k) { ax[k] = 0; aw[k] = 0; axs[k] = 0; axc[k] = 0; aws[k] = 0; awc[k] = 0; }
     sxx = sxw = sww = 0;
+    fxx[0] = fxx[1] = fxw[0] = fxw[1] = fww[0] = fww[1] = 0.f;
+  }
+
+  // self-term accumulation: float64 products in the float64 form; float
+  // products with Kahan compensation in the float32 form (no FP64 pipe use)
+  __device__ __forceinline__ void self_add(int which, Tc a, Tc b) {
+    if constexpr (F64) {
+      double p = (double)a * (double)b;
+      if (which == 0) sxx += p; else if (which == 1) sxw += p; else sww += p;
+    } else {
+      float p = (float)a * (float)b;
+      if (which == 0) kahan(fxx[0], fxx[1], p);
+      else if (which == 1) kahan(fxw[0], fxw[1], p);
+      else kahan(fww[0], fww[1], p);
+    }
   }
 
   __device__ __forceinline__ static void kahan(float& s, float& c, float v) {
@@ -132,24 +148,41 @@ struct Engine {
         else x[u] = a * (Tc)__ldcg(ps.srcB + gi[u]);
       }
     }
-    // x -= sum_c coef_c V_c : one coefficient load per column, applied to all points
+    // x -= sum_c coef_c V_c : one coefficient load per column, applied to all
+    // points; loads are issued in batches of CB columns before their FMAs so
+    // that several round trips to L2/HBM overlap, and two accumulators per
+    // point halve the FMA dependency chain.
+    constexpr int CB = F64 ? 4 : 8;
+    Tc xb[QP];
+#pragma unroll
+    for (int u = 0; u < QP; ++u) xb[u] = (Tc)0;
     int c = ps.c0;
-    for (; c + 2 <= ps.c1; c += 2) {
-      const Tc c0 = S.coefc[c], c1 = S.coefc[c + 1];
-      const B* col0 = Vb + (long long)c * N;
-      const B* col1 = col0 + N;
-      Tc v0[QP], v1[QP];
+    for (; c + CB <= ps.c1; c += CB) {
+      Tc v[CB][QP];
 #pragma unroll
-      for (int u = 0; u < QP; ++u) { v0[u] = (Tc)__ldcg(col0 + gi[u]); v1[u] = (Tc)__ldcg(col1 + gi[u]); }
+      for (int i = 0; i < CB; ++i) {
+        const B* col = Vb + (long long)(c + i) * N;
 #pragma unroll
-      for (int u = 0; u < QP; ++u) { x[u] = fma(-c0, v0[u], x[u]); x[u] = fma(-c1, v1[u], x[u]); }
+        for (int u = 0; u < QP; ++u) v[i][u] = (Tc)__ldcg(col + gi[u]);
+      }
+#pragma unroll
+      for (int i = 0; i < CB; ++i) {
+        const Tc cc = S.coefc[c + i];
+#pragma unroll
+        for (int u = 0; u < QP; ++u) {
+          if (i & 1) xb[u] = fma(-cc, v[i][u], xb[u]);
+          else x[u] = fma(-cc, v[i][u], x[u]);
+        }
+      }
     }
-    if (c < ps.c1) {
-      const Tc c0 = S.coefc[c];
-      const B* col0 = Vb + (long long)c * N;
+    for (; c < ps.c1; ++c) {
+      const Tc cc = S.coefc[c];
+      const B* col = Vb + (long long)c * N;
 #pragma unroll
-      for (int u = 0; u < QP; ++u) x[u] = fma(-c0, (Tc)__ldcg(col0 + gi[u]), x[u]);
+      for (int u = 0; u < QP; ++u) x[u] = fma(-cc, (Tc)__ldcg(col + gi[u]), x[u]);
     }
+#pragma unroll
+    for (int u = 0; u < QP; ++u) x[u] += xb[u];
 #pragma unroll
     for (int u = 0; u < QP; ++u) {
       if (so[u] < 0) continue;
@@ -158,7 +191,7 @@ struct Engine {
       ring[so[u] & ((1 << 30) - 1)] = xv;
       if (so[u] & (1 << 30)) {
         if (ps.xout) ps.xout[gi[u]] = (B)xv;
-        if (!ps.wout && (ps.self & SELF_XX)) sxx += (double)xv * (double)xv;
+        if (!ps.wout && (ps.self & SELF_XX)) self_add(0, xv, xv);
       }
     }
   }
@@ -181,10 +214,10 @@ struct Engine {
       if constexpr (!F64) wv = (Tc)(B)wv;
       S.wbuf[s * TX * TY + tid] = wv;
       ps.wout[s * d.npts + gpt] = (B)wv;
-      double xd = (double)z0[s * PS + o], wd = (double)wv;
-      if (ps.self & SELF_XX) sxx += xd * xd;
-      if (ps.self & SELF_XW) sxw += xd * wd;
-      if (ps.self & SELF_WW) sww += wd * wd;
+      const Tc xs = z0[s * PS + o];
+      if (ps.self & SELF_XX) self_add(0, xs, xs);
+      if (ps.self & SELF_XW) self_add(1, xs, wv);
+      if (ps.self & SELF_WW) self_add(2, wv, wv);
     }
   }
 
@@ -214,35 +247,46 @@ struct Engine {
           xv[k] = 0; wv[k] = 0; gi[k] = 0;
         }
       }
+      // columns of this warp: c = d0 + warp + NW*kk; the next column's values
+      // are loaded while the current one is consumed
+      Tc vb[2][NPS];
+      {
+        const int c = ps.d0 + warp;
+        const B* base = Vc(c < ps.d1 ? c : ps.d0);
+#pragma unroll
+        for (int k = 0; k < NPS; ++k) vb[0][k] = (Tc)__ldcg(base + gi[k]);
+      }
 #pragma unroll
       for (int kk = 0; kk < KMAX; ++kk) {
-        int c = ps.d0 + warp + NW * kk;
-        if (c < ps.d1) {
-          const B* base = Vc(c);
-          if constexpr (F64) {
-            double px0 = 0, pw0 = 0, px1 = 0, pw1 = 0;   // two chains each: more FP64 ILP
+        const int c = ps.d0 + warp + NW * kk;
+        if (c >= ps.d1) break;
+        const int cn = c + NW;
+        if (kk + 1 < KMAX && cn < ps.d1) {
+          const B* nb = Vc(cn);
 #pragma unroll
-            for (int k = 0; k < NPS; k += 2) {
-              double v0 = (double)__ldcg(base + gi[k]);
-              double v1 = (double)__ldcg(base + gi[k + 1]);
-              px0 = fma(v0, (double)xv[k], px0);
-              pw0 = fma(v0, (double)wv[k], pw0);
-              px1 = fma(v1, (double)xv[k + 1], px1);
-              pw1 = fma(v1, (double)wv[k + 1], pw1);
-            }
-            if (dx) ax[kk] += px0 + px1;
-            if (dw) aw[kk] += pw0 + pw1;
-          } else {
-            float px = 0.f, pw = 0.f;
+          for (int k = 0; k < NPS; ++k) vb[(kk + 1) & 1][k] = (Tc)__ldcg(nb + gi[k]);
+        }
+        const Tc* v = vb[kk & 1];
+        if constexpr (F64) {
+          double px0 = 0, pw0 = 0, px1 = 0, pw1 = 0;   // two chains each: more FP64 ILP
 #pragma unroll
-            for (int k = 0; k < NPS; ++k) {
-              float v = (float)__ldcg(base + gi[k]);
-              px = fmaf(v, (float)xv[k], px);
-              pw = fmaf(v, (float)wv[k], pw);
-            }
-            if (dx) kahan(axs[kk], axc[kk], px);
-            if (dw) kahan(aws[kk], awc[kk], pw);
+          for (int k = 0; k < NPS; k += 2) {
+            px0 = fma((double)v[k], (double)xv[k], px0);
+            pw0 = fma((double)v[k], (double)wv[k], pw0);
+            px1 = fma((double)v[k + 1], (double)xv[k + 1], px1);
+            pw1 = fma((double)v[k + 1], (double)wv[k + 1], pw1);
           }
+          if (dx) ax[kk] += px0 + px1;
+          if (dw) aw[kk] += pw0 + pw1;
+        } else {
+          float px = 0.f, pw = 0.f;
+#pragma unroll
+          for (int k = 0; k < NPS; ++k) {
+            px = fmaf((float)v[k], (float)xv[k], px);
+            pw = fmaf((float)v[k], (float)wv[k], pw);
+          }
+          if (dx) kahan(axs[kk], axc[kk], px);
+          if (dw) kahan(aws[kk], awc[kk], pw);
         }
       }
     }
@@ -302,6 +346,11 @@ struct Engine {
         part[c - ps.d0] = (ps.dmode & DOT_X) ? vx : 0.0;
         part[nd + c - ps.d0] = (ps.dmode & DOT_W) ? vw : 0.0;
       }
+    }
+    if constexpr (!F64) {
+      sxx = (double)fxx[0] - (double)fxx[1];
+      sxw = (double)fxw[0] - (double)fxw[1];
+      sww = (double)fww[0] - (double)fww[1];
     }
     double a0 = warp_sum(sxx), a1 = warp_sum(sxw), a2 = warp_sum(sww);
     if (lane == 0) { S.bred[warp][0] = a0; S.bred[warp][1] = a1; S.bred[warp][2] = a2; }
@@ -763,8 +812,16 @@ struct Engine {
   }
 };
 
+#ifndef LSA_MINB_F64
+#define LSA_MINB_F64 2
+#endif
+#ifndef LSA_MINB_F32
+#define LSA_MINB_F32 2
+#endif
+
 template <class Op, class Tc, class B>
-__global__ void __launch_bounds__(NT, 2) k_arnoldi(ArnoldiParams P) {
+__global__ void __launch_bounds__(NT, (sizeof(Tc) == 8) ? LSA_MINB_F64 : LSA_MINB_F32)
+    k_arnoldi(ArnoldiParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   using E = Engine<Op, Tc, B>;
   typename E::Smem& S = *reinterpret_cast<typename E::Smem*>(smem_raw);
