@@ -1,6 +1,7 @@
 // C-ABI entry points of liblsarnoldi: argument checks, workspace layout and
 // the launch sequence of each call.  See include/lsarnoldi.h for the contract.
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include "lsa_internal.cuh"
@@ -16,6 +17,12 @@ cudaError_t launch_matvec_adr3d(const ArnoldiParams&, int, const void*, void*, i
 int blocks_per_sm_advdiff2d(int);
 int blocks_per_sm_grayscott2d(int);
 int blocks_per_sm_adr3d(int);
+bool tma_applicable_advdiff2d(const DevOp&, const Tiling&, int, int);
+bool tma_applicable_grayscott2d(const DevOp&, const Tiling&, int, int);
+bool tma_applicable_adr3d(const DevOp&, const Tiling&, int, int);
+cudaError_t launch_arnoldi_tma_advdiff2d(const ArnoldiParams&, int, int, cudaStream_t);
+cudaError_t launch_arnoldi_tma_grayscott2d(const ArnoldiParams&, int, int, cudaStream_t);
+cudaError_t launch_arnoldi_tma_adr3d(const ArnoldiParams&, int, int, cudaStream_t);
 
 static const long long kTimeoutNs = 5000000000LL;   // 5 s per barrier wait
 static const double kBreakdownTolFp64 = 1e-13;
@@ -77,7 +84,11 @@ Tiling make_tiling(const DevOp& d) {
   Tiling t;
   t.tiles_x = (d.nx + TX - 1) / TX;
   t.tiles_y = (d.ny + TY - 1) / TY;
-  t.ZS = (d.kind == LSA_OP_ADR3D) ? (d.nz < 32 ? d.nz : 32) : 1;
+  // z-segment: the largest divisor of nz that is at most 32 (uniform segments)
+  t.ZS = 1;
+  if (d.kind == LSA_OP_ADR3D)
+    for (int z = (d.nz < 32 ? d.nz : 32); z >= 1; --z)
+      if (d.nz % z == 0) { t.ZS = z; break; }
   t.zsegs = (d.nz + t.ZS - 1) / t.ZS;
   t.ntiles = t.tiles_x * t.tiles_y * t.zsegs;
   return t;
@@ -105,7 +116,27 @@ int arnoldi_blocks_per_sm(const DevOp& d, int precision) {
   return nb;
 }
 
+// The TMA-staged kernel runs the hybrid variants of the float32-basis form
+// whenever its stage buffers fit in shared memory and the grid meets the TMA
+// alignment rules (LSA_TMA=0 in the environment disables it, LSA_TMA=1 also
+// allows it for the float64 form).
+static bool use_tma(const ArnoldiParams& P, int precision) {
+  if (P.variant < LSA_HCWY) return false;
+  const char* env = getenv("LSA_TMA");
+  if (env && env[0] == '0') return false;
+  if (precision == LSA_FP64 && !(env && env[0] == '1')) return false;
+  if (P.op.kind == LSA_OP_ADVDIFF2D) return tma_applicable_advdiff2d(P.op, P.tl, P.m, precision);
+  if (P.op.kind == LSA_OP_GRAYSCOTT2D) return tma_applicable_grayscott2d(P.op, P.tl, P.m, precision);
+  return tma_applicable_adr3d(P.op, P.tl, P.m, precision);
+}
+
 cudaError_t launch_arnoldi(const ArnoldiParams& P, int precision, int G, cudaStream_t s) {
+  if (use_tma(P, precision)) {
+    const int maxG = sm_count() * 2;
+    if (P.op.kind == LSA_OP_ADVDIFF2D) return launch_arnoldi_tma_advdiff2d(P, precision, maxG, s);
+    if (P.op.kind == LSA_OP_GRAYSCOTT2D) return launch_arnoldi_tma_grayscott2d(P, precision, maxG, s);
+    return launch_arnoldi_tma_adr3d(P, precision, maxG, s);
+  }
   if (P.op.kind == LSA_OP_ADVDIFF2D) return launch_arnoldi_advdiff2d(P, precision, G, s);
   if (P.op.kind == LSA_OP_GRAYSCOTT2D) return launch_arnoldi_grayscott2d(P, precision, G, s);
   return launch_arnoldi_adr3d(P, precision, G, s);
@@ -132,13 +163,15 @@ static bool make_layout(const DevOp& d, int m, int precision, Layout* L) {
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
   L->ctl = take(sizeof(Ctl));
-  L->partials = take((size_t)sms * bps * SLOTS * sizeof(double));
+  L->partials = take((size_t)sms * (bps > 2 ? bps : 2) * SLOTS * sizeof(double));
   L->T = take((size_t)MMAX * MMAX * sizeof(double));
   L->L = take((size_t)MMAX * MMAX * sizeof(double));
   L->H = take((size_t)(m + 1) * m * sizeof(double));
-  L->V = take((size_t)d.N * (m + 1) * bsz);
-  L->W0 = take((size_t)d.N * bsz);
-  L->W1 = take((size_t)d.N * bsz);
+  // basis columns 0..m and the two matvec buffers as columns m+1, m+2 of one
+  // contiguous block (one tensor for the TMA-staged kernel)
+  L->V = take((size_t)d.N * (m + 3) * bsz);
+  L->W0 = L->V + (size_t)d.N * (m + 1) * bsz;
+  L->W1 = L->V + (size_t)d.N * (m + 2) * bsz;
   L->small = take((size_t)6 * SMALL_STRIDE * SMALL_STRIDE * sizeof(double));
   L->coefs = take((size_t)(PMAX + 2) * (MMAX + 2) * sizeof(double));
   size_t nfield = 0;
@@ -285,7 +318,8 @@ lsa_status lsa_matvec(const lsa_op* op, const void* x, void* y, int precision, v
   lsa_status st = prepare(op, 1, precision, work, work_bytes, &pr);
   if (st != LSA_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = launch_init(pr.P.ctl, pr.d, (float*)pr.d.g0, (float*)pr.d.g1, precision, nullptr, 0, s);
+  cudaError_t e = launch_init(pr.P.ctl, pr.d, (float*)pr.d.g0, (float*)pr.d.g1, precision, nullptr, 0,
+                              nullptr, nullptr, s);
   if (e == cudaSuccess) e = launch_matvec(pr.P, precision, x, y, pr.L.G, s);
   return from_cuda(e);
 }
@@ -303,22 +337,22 @@ lsa_status lsa_arnoldi(const lsa_op* op, const double* v, int m, int variant, in
   cudaStream_t s = (cudaStream_t)stream;
   ArnoldiParams P = pr.P;
   P.vin = v;
-  P.V = V;
   P.H = H;
   P.variant = variant;
   P.write_vlast = 1;
   CallTimer tm(stats != nullptr, s);
   cudaError_t e = launch_init(P.ctl, pr.d, (float*)pr.d.g0, (float*)pr.d.g1, precision, H,
-                              (m + 1) * m, s);
+                              (m + 1) * m, v, P.V, s);
   tm.mark(0);
   if (e == cudaSuccess) e = launch_arnoldi(P, precision, pr.L.G, s);
   tm.mark(1);
-  if (e == cudaSuccess && variant >= LSA_HCWY) e = launch_scale_basis(V, precision, N, m, P.ctl, s);
+  if (e == cudaSuccess)
+    e = launch_copy_basis(V, P.V, precision, N, m, P.ctl, variant >= LSA_HCWY ? 1 : 0, s);
   if (e != cudaSuccess) return LSA_ERR_CUDA;
   if (stats) {
     lsa_status r = fill_stats(P.ctl, stats, s);
     stats->ms_arnoldi = tm.ms(0, 1);
-    stats->launches = variant >= LSA_HCWY ? 3 : 2;
+    stats->launches = 3;
     return r;
   }
   return LSA_OK;
@@ -343,7 +377,7 @@ lsa_status lsa_phiv(const lsa_op* op, const double* v, double h, int p, int m, d
   P.write_vlast = 0;
   CallTimer tm(stats != nullptr, s);
   cudaError_t e = launch_init(P.ctl, pr.d, (float*)pr.d.g0, (float*)pr.d.g1, precision, P.H,
-                              (m + 1) * m, s);
+                              (m + 1) * m, v, P.V, s);
   tm.mark(0);
   if (e == cudaSuccess) e = launch_arnoldi(P, precision, pr.L.G, s);
   tm.mark(1);

@@ -1,6 +1,6 @@
 // Arnoldi kernels instantiated for the adr3d operator (one translation unit
 // per operator so that the library builds in parallel).
-#include "lsa_engine.cuh"
+#include "lsa_tma.cuh"
 
 namespace lsa {
 
@@ -12,5 +12,13 @@ cudaError_t launch_matvec_adr3d(const ArnoldiParams& P, int precision, const voi
   return launch_matvec_op<OpADR3D>(P, precision, x, y, G, s);
 }
 int blocks_per_sm_adr3d(int precision) { return blocks_per_sm_op<OpADR3D>(precision); }
+bool tma_applicable_adr3d(const DevOp& d, const Tiling& tl, int m, int precision) {
+  return precision == LSA_FP32_BASIS ? tma_applicable_op<OpADR3D, float>(d, tl, m)
+                                     : tma_applicable_op<OpADR3D, double>(d, tl, m);
+}
+cudaError_t launch_arnoldi_tma_adr3d(const ArnoldiParams& P, int precision, int maxG, cudaStream_t s) {
+  return precision == LSA_FP32_BASIS ? launch_arnoldi_tma_op<OpADR3D, float>(P, maxG, s)
+                                     : launch_arnoldi_tma_op<OpADR3D, double>(P, maxG, s);
+}
 
 }  // namespace lsa

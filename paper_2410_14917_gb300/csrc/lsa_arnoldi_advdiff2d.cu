@@ -1,6 +1,6 @@
 // Arnoldi kernels instantiated for the advdiff2d operator (one translation unit
 // per operator so that the library builds in parallel).
-#include "lsa_engine.cuh"
+#include "lsa_tma.cuh"
 
 namespace lsa {
 
@@ -12,5 +12,13 @@ cudaError_t launch_matvec_advdiff2d(const ArnoldiParams& P, int precision, const
   return launch_matvec_op<OpAdvDiff2D>(P, precision, x, y, G, s);
 }
 int blocks_per_sm_advdiff2d(int precision) { return blocks_per_sm_op<OpAdvDiff2D>(precision); }
+bool tma_applicable_advdiff2d(const DevOp& d, const Tiling& tl, int m, int precision) {
+  return precision == LSA_FP32_BASIS ? tma_applicable_op<OpAdvDiff2D, float>(d, tl, m)
+                                     : tma_applicable_op<OpAdvDiff2D, double>(d, tl, m);
+}
+cudaError_t launch_arnoldi_tma_advdiff2d(const ArnoldiParams& P, int precision, int maxG, cudaStream_t s) {
+  return precision == LSA_FP32_BASIS ? launch_arnoldi_tma_op<OpAdvDiff2D, float>(P, maxG, s)
+                                     : launch_arnoldi_tma_op<OpAdvDiff2D, double>(P, maxG, s);
+}
 
 }  // namespace lsa

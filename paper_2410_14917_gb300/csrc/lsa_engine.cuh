@@ -49,7 +49,6 @@ struct Engine {
     Tc coefc[MMAX + 2];
     double red[SLOTS];
     double tmp[4][MMAX + 2];
-    double small[MMAX * MMAX];
     double bred[NW][3];
     double sj, scale, true_nrm, ss;
     Tc a;
@@ -58,16 +57,19 @@ struct Engine {
 
   const ArnoldiParams& P;
   Smem& S;
+  double* small;                     // MMAX x MMAX scratch of the last-arriving CTA
   Coef<Tc> cf;
   const int tid, lane, warp;
+  __host__ __device__ static constexpr size_t small_offset() { return (sizeof(Smem) + 127) & ~(size_t)127; }
+  __host__ __device__ static constexpr size_t smem_bytes() { return small_offset() + sizeof(double) * MMAX * MMAX; }
   // dot accumulators (per lane)
   double ax[KMAX], aw[KMAX];
   float axs[KMAX], axc[KMAX], aws[KMAX], awc[KMAX];
   double sxx, sxw, sww;              // self terms (float64 form)
   float fxx[2], fxw[2], fww[2];      // self terms (float32 form): Kahan sum, compensation
 
-  __device__ Engine(const ArnoldiParams& p, Smem& s)
-      : P(p), S(s), tid(threadIdx.x), lane(threadIdx.x & 31), warp(threadIdx.x >> 5) {
+  __device__ Engine(const ArnoldiParams& p, Smem& s, double* sm)
+      : P(p), S(s), small(sm), tid(threadIdx.x), lane(threadIdx.x & 31), warp(threadIdx.x >> 5) {
     cf.load(P.op);
   }
 
@@ -331,7 +333,11 @@ struct Engine {
         }
       }
     }
-    // write this CTA's partials
+    return write_partials(ps);
+  }
+
+  // Per-CTA partial sums of a pass to HBM (dot slots, then the three self terms).
+  __device__ int write_partials(const PassT<B>& ps) {
     const int nd = ps.d1 > ps.d0 ? ps.d1 - ps.d0 : 0;
     double* part = P.partials + (long long)blockIdx.x * SLOTS;
 #pragma unroll
@@ -480,8 +486,8 @@ struct Engine {
       for (int k = tid; k < np; k += NT) {
         double acc = -temp1[k];
         if (P.variant != LSA_HNCWY)
-          for (int i = k + 1; i < np; ++i) acc = fma(-temp1[i], S.small[i * MMAX + k], acc);
-        S.small[np * MMAX + k] = acc;
+          for (int i = k + 1; i < np; ++i) acc = fma(-temp1[i], small[i * MMAX + k], acc);
+        small[np * MMAX + k] = acc;
         P.T[np * MMAX + k] = acc;
       }
       __syncthreads();
@@ -493,20 +499,20 @@ struct Engine {
         apply_unit_lower(temp2, aux, j);                  // aux = y
         stage(P.L, np);
         for (int k = tid; k < np; k += NT) {
-          S.small[np * MMAX + k] = temp1[k];
+          small[np * MMAX + k] = temp1[k];
           P.L[np * MMAX + k] = temp1[k];
         }
         __syncthreads();
         for (int r = tid; r < j; r += NT) {
           double acc = 0.0;
-          for (int k = r + 1; k < j; ++k) acc = fma(S.small[k * MMAX + r], aux[k], acc);
+          for (int k = r + 1; k < j; ++k) acc = fma(small[k * MMAX + r], aux[k], acc);
           hcol[r] = temp2[r] - acc;
         }
         __syncthreads();
         if (warp == 0) {                                   // forward substitution
           for (int r = 0; r < j; ++r) {
             double acc = 0.0;
-            for (int k = lane; k < r; k += 32) acc = fma(S.small[r * MMAX + k], hcol[k], acc);
+            for (int k = lane; k < r; k += 32) acc = fma(small[r * MMAX + k], hcol[k], acc);
             acc = warp_sum(acc);
             if (lane == 0) hcol[r] = hcol[r] - acc;
             __syncwarp();
@@ -558,7 +564,7 @@ struct Engine {
   __device__ void stage(const double* M, int rows) {
     for (int e = tid; e < rows * MMAX; e += NT) {
       int r = e / MMAX, k = e - r * MMAX;
-      if (k < r) S.small[e] = __ldcg(M + e);
+      if (k < r) small[e] = __ldcg(M + e);
     }
     __syncthreads();
   }
@@ -567,7 +573,7 @@ struct Engine {
   __device__ void apply_unit_lower(const double* in, double* out, int n) {
     for (int r = warp; r < n; r += NW) {
       double acc = 0.0;
-      for (int k = lane; k < r; k += 32) acc = fma(S.small[r * MMAX + k], in[k], acc);
+      for (int k = lane; k < r; k += 32) acc = fma(small[r * MMAX + k], in[k], acc);
       acc = warp_sum(acc);
       if (lane == 0) out[r] = in[r] + acc;
     }
@@ -825,7 +831,7 @@ __global__ void __launch_bounds__(NT, (sizeof(Tc) == 8) ? LSA_MINB_F64 : LSA_MIN
   extern __shared__ __align__(16) unsigned char smem_raw[];
   using E = Engine<Op, Tc, B>;
   typename E::Smem& S = *reinterpret_cast<typename E::Smem*>(smem_raw);
-  E e(P, S);
+  E e(P, S, reinterpret_cast<double*>(smem_raw + E::small_offset()));
   if (P.variant == LSA_MGS) e.run_mgs(P.write_vlast != 0);
   else if (P.variant == LSA_CGS2) e.run_cgs2(P.write_vlast != 0);
   else e.run_hybrid();
@@ -837,7 +843,7 @@ __global__ void __launch_bounds__(NT) k_matvec(ArnoldiParams P, const B* x, B* y
   extern __shared__ __align__(16) unsigned char smem_raw[];
   using E = Engine<Op, Tc, B>;
   typename E::Smem& S = *reinterpret_cast<typename E::Smem*>(smem_raw);
-  E e(P, S);
+  E e(P, S, reinterpret_cast<double*>(smem_raw + E::small_offset()));
   if (threadIdx.x == 0) S.a = (Tc)1;
   __syncthreads();
   PassT<B> ps;
@@ -852,13 +858,13 @@ cudaError_t launch_arnoldi_op(const ArnoldiParams& P, int precision, int G, cuda
   void* args[1] = {&Pc};
   if (precision == LSA_FP64) {
     auto k = k_arnoldi<Op, double, double>;
-    size_t sm = sizeof(typename Engine<Op, double, double>::Smem);
+    size_t sm = Engine<Op, double, double>::smem_bytes();
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     return cudaLaunchCooperativeKernel((void*)k, dim3(G), dim3(NT), args, sm, s);
   } else {
     auto k = k_arnoldi<Op, float, float>;
-    size_t sm = sizeof(typename Engine<Op, float, float>::Smem);
+    size_t sm = Engine<Op, float, float>::smem_bytes();
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     return cudaLaunchCooperativeKernel((void*)k, dim3(G), dim3(NT), args, sm, s);
@@ -870,13 +876,13 @@ cudaError_t launch_matvec_op(const ArnoldiParams& P, int precision, const void* 
                              cudaStream_t s) {
   if (precision == LSA_FP64) {
     auto k = k_matvec<Op, double, double>;
-    size_t sm = sizeof(typename Engine<Op, double, double>::Smem);
+    size_t sm = Engine<Op, double, double>::smem_bytes();
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     k<<<G, NT, sm, s>>>(P, (const double*)x, (double*)y);
   } else {
     auto k = k_matvec<Op, float, float>;
-    size_t sm = sizeof(typename Engine<Op, float, float>::Smem);
+    size_t sm = Engine<Op, float, float>::smem_bytes();
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     k<<<G, NT, sm, s>>>(P, (const float*)x, (float*)y);
@@ -889,12 +895,12 @@ int blocks_per_sm_op(int precision) {
   int nb = 0;
   if (precision == LSA_FP64) {
     auto k = k_arnoldi<Op, double, double>;
-    size_t sm = sizeof(typename Engine<Op, double, double>::Smem);
+    size_t sm = Engine<Op, double, double>::smem_bytes();
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, NT, sm);
   } else {
     auto k = k_arnoldi<Op, float, float>;
-    size_t sm = sizeof(typename Engine<Op, float, float>::Smem);
+    size_t sm = Engine<Op, float, float>::smem_bytes();
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, NT, sm);
   }

@@ -4,7 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/lsarnoldi.h"
+#include "lsarnoldi.h"
 
 namespace lsa {
 
@@ -128,9 +128,9 @@ cudaError_t launch_expm(const SmallParams& P, cudaStream_t s);
 cudaError_t launch_combine(const void* V, int precision, long long N, const double* C, int ldc,
                            int p, const Ctl* ctl, double* y, cudaStream_t s);
 cudaError_t launch_init(Ctl* ctl, const DevOp& op, float* g0, float* g1, int precision,
-                        double* H, int ldh_total, cudaStream_t s);
-cudaError_t launch_scale_basis(void* V, int precision, long long N, int m, const Ctl* ctl,
-                               cudaStream_t s);
+                        double* H, int ldh_total, const double* vin, void* vcol0, cudaStream_t s);
+cudaError_t launch_copy_basis(void* Vdst, const void* Vsrc, int precision, long long N, int m,
+                              const Ctl* ctl, int apply_sigma, cudaStream_t s);
 cudaError_t launch_timeout_selftest(Ctl* ctl, long long timeout_ns, cudaStream_t s);
 
 // ---------------------------------------------------------------------------

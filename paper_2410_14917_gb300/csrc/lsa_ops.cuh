@@ -23,11 +23,10 @@ struct Coef {
 
 // 2D periodic advection-diffusion: A v = c Lap5 v - u.grad v (central).
 struct OpAdvDiff2D {
-  static constexpr int NS = 1, DIM = 2, KIND = LSA_OP_ADVDIFF2D;
+  static constexpr int NS = 1, DIM = 2, KIND = LSA_OP_ADVDIFF2D, NF = 0;
   template <class Tc>
-  __device__ __forceinline__ static void apply(const DevOp&, const Coef<Tc>& c, const Tc* zm,
-                                               const Tc* z0, const Tc* zp, int o, long long,
-                                               Tc* out) {
+  __device__ __forceinline__ static void apply_f(const Coef<Tc>& c, const Tc* zm, const Tc* z0,
+                                                 const Tc* zp, int o, Tc, Tc, Tc* out) {
     (void)zm; (void)zp;
     Tc x = z0[o];
     Tc r = c.cC * x;
@@ -37,47 +36,51 @@ struct OpAdvDiff2D {
     r = fma(c.cN, z0[o + PW], r);
     out[0] = r;
   }
+  template <class Tc>
+  __device__ __forceinline__ static void apply(const DevOp&, const Coef<Tc>& c, const Tc* zm,
+                                               const Tc* z0, const Tc* zp, int o, long long,
+                                               Tc* out) {
+    apply_f<Tc>(c, zm, z0, zp, o, (Tc)0, (Tc)0, out);
+  }
 };
 
-// Jacobian of 2D Gray-Scott at (u0, v0), species-major [u; v].
+// Jacobian of 2D Gray-Scott at (u0, v0), species-major [u; v].  Field values:
+// (u0, v0) in the float64 form, the float copies (a, b) = (v0^2, 2 u0 v0) in the
+// float32 form.
 struct OpGrayScott2D {
-  static constexpr int NS = 2, DIM = 2, KIND = LSA_OP_GRAYSCOTT2D;
+  static constexpr int NS = 2, DIM = 2, KIND = LSA_OP_GRAYSCOTT2D, NF = 2;
   template <class Tc>
-  __device__ __forceinline__ static void apply(const DevOp& d, const Coef<Tc>& c, const Tc* zm,
-                                               const Tc* z0, const Tc* zp, int o, long long gpt,
-                                               Tc* out) {
+  __device__ __forceinline__ static void apply_f(const Coef<Tc>& c, const Tc* zm, const Tc* z0,
+                                                 const Tc* zp, int o, Tc f0, Tc f1, Tc* out) {
     (void)zm; (void)zp;
-    Tc a, b;  // a = v0^2, b = 2 u0 v0
-    if constexpr (sizeof(Tc) == 8) {
-      double u0 = __ldg(d.f0 + gpt), v0 = __ldg(d.f1 + gpt);
-      a = v0 * v0;
-      b = 2.0 * u0 * v0;
-    } else {
-      a = __ldg(d.g0 + gpt);
-      b = __ldg(d.g1 + gpt);
-    }
+    Tc a, b;
+    if constexpr (sizeof(Tc) == 8) { a = f1 * f1; b = (Tc)2 * f0 * f1; }
+    else { a = f0; b = f1; }
     const Tc* U = z0;
     const Tc* Vv = z0 + PS;
     Tc u = U[o], v = Vv[o];
     Tc lu = (U[o - 1] + U[o + 1]) + (U[o - PW] + U[o + PW]) - (Tc)4 * u;
     Tc lv = (Vv[o - 1] + Vv[o + 1]) + (Vv[o - PW] + Vv[o + PW]) - (Tc)4 * v;
-    Tc ru = c.du * lu - (a + c.F) * u - b * v;
-    Tc rv = c.dv * lv + (b - c.F - c.k) * v + a * u;
-    out[0] = ru;
-    out[1] = rv;
+    out[0] = c.du * lu - (a + c.F) * u - b * v;
+    out[1] = c.dv * lv + (b - c.F - c.k) * v + a * u;
+  }
+  template <class Tc>
+  __device__ __forceinline__ static void apply(const DevOp& d, const Coef<Tc>& c, const Tc* zm,
+                                               const Tc* z0, const Tc* zp, int o, long long gpt,
+                                               Tc* out) {
+    Tc f0, f1;
+    if constexpr (sizeof(Tc) == 8) { f0 = __ldg(d.f0 + gpt); f1 = __ldg(d.f1 + gpt); }
+    else { f0 = __ldg(d.g0 + gpt); f1 = __ldg(d.g1 + gpt); }
+    apply_f<Tc>(c, zm, z0, zp, o, f0, f1, out);
   }
 };
 
 // 3D periodic advection-diffusion-reaction with first-order upwinding.
 struct OpADR3D {
-  static constexpr int NS = 1, DIM = 3, KIND = LSA_OP_ADR3D;
+  static constexpr int NS = 1, DIM = 3, KIND = LSA_OP_ADR3D, NF = 1;
   template <class Tc>
-  __device__ __forceinline__ static void apply(const DevOp& d, const Coef<Tc>& c, const Tc* zm,
-                                               const Tc* z0, const Tc* zp, int o, long long gpt,
-                                               Tc* out) {
-    Tc rr;
-    if constexpr (sizeof(Tc) == 8) rr = __ldg(d.f0 + gpt);
-    else rr = __ldg(d.g0 + gpt);
+  __device__ __forceinline__ static void apply_f(const Coef<Tc>& c, const Tc* zm, const Tc* z0,
+                                                 const Tc* zp, int o, Tc rr, Tc, Tc* out) {
     Tc x = z0[o];
     Tc r = (c.cC + rr) * x;
     r = fma(c.cW, z0[o - 1], r);
@@ -87,6 +90,15 @@ struct OpADR3D {
     r = fma(c.cD, zm[o], r);
     r = fma(c.cU, zp[o], r);
     out[0] = r;
+  }
+  template <class Tc>
+  __device__ __forceinline__ static void apply(const DevOp& d, const Coef<Tc>& c, const Tc* zm,
+                                               const Tc* z0, const Tc* zp, int o, long long gpt,
+                                               Tc* out) {
+    Tc rr;
+    if constexpr (sizeof(Tc) == 8) rr = __ldg(d.f0 + gpt);
+    else rr = __ldg(d.g0 + gpt);
+    apply_f<Tc>(c, zm, z0, zp, o, rr, (Tc)0, out);
   }
 };
 

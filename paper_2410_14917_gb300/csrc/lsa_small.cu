@@ -12,12 +12,18 @@ namespace lsa {
 // float copies of the coefficient fields used by the stencil.
 
 __global__ void k_init(Ctl* ctl, DevOp op, float* g0, float* g1, int precision, double* H,
-                       int hcount) {
+                       int hcount, const double* vin, void* vcol0) {
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long stride = (long long)gridDim.x * blockDim.x;
   const int nctl = (int)(sizeof(Ctl) / sizeof(int));
   for (long long i = tid; i < nctl; i += stride) reinterpret_cast<int*>(ctl)[i] = 0;
   for (long long i = tid; i < hcount; i += stride) H[i] = 0.0;
+  if (vin && vcol0) {   // basis column 0 holds the start vector (in the basis type)
+    if (precision == LSA_FP64)
+      for (long long i = tid; i < op.N; i += stride) reinterpret_cast<double*>(vcol0)[i] = vin[i];
+    else
+      for (long long i = tid; i < op.N; i += stride) reinterpret_cast<float*>(vcol0)[i] = (float)vin[i];
+  }
   if (precision == LSA_FP32_BASIS) {
     if (op.kind == LSA_OP_GRAYSCOTT2D) {
       long long n = op.nx * (long long)op.ny;
@@ -33,11 +39,11 @@ __global__ void k_init(Ctl* ctl, DevOp op, float* g0, float* g1, int precision, 
 }
 
 cudaError_t launch_init(Ctl* ctl, const DevOp& op, float* g0, float* g1, int precision, double* H,
-                        int hcount, cudaStream_t s) {
+                        int hcount, const double* vin, void* vcol0, cudaStream_t s) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  k_init<<<sms * 4, 256, 0, s>>>(ctl, op, g0, g1, precision, H, hcount);
+  k_init<<<sms * 4, 256, 0, s>>>(ctl, op, g0, g1, precision, H, hcount, vin, vcol0);
   return cudaGetLastError();
 }
 
@@ -274,13 +280,16 @@ __global__ void __launch_bounds__(256) k_combine(const B* __restrict__ V, long l
                                                  const double* __restrict__ C, int ldc, int p,
                                                  const Ctl* ctl, double* __restrict__ y) {
   __shared__ double cs[(PMAX + 1) * (MMAX + 2)];
+  __shared__ float csf[(PMAX + 1) * (MMAX + 2)];   // float copies: no FP64 pipe in the float form
   __shared__ int sm;
   if (threadIdx.x == 0) sm = __ldcg(&ctl->m_eff) * (__ldcg(&ctl->status) >= 0);
   __syncthreads();
   const int m = sm;
   for (int i = threadIdx.x; i < (p + 1) * m; i += blockDim.x) {
     int k = i / m, c = i - k * m;
-    cs[k * (MMAX + 2) + c] = __ldg(C + (long long)k * ldc + c);
+    const double v = __ldg(C + (long long)k * ldc + c);
+    cs[k * (MMAX + 2) + c] = v;
+    csf[k * (MMAX + 2) + c] = (float)v;
   }
   __syncthreads();
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -306,7 +315,7 @@ __global__ void __launch_bounds__(256) k_combine(const B* __restrict__ V, long l
         float v = __ldg(V + (long long)i * N + e);
 #pragma unroll
         for (int k = 0; k <= PP; ++k)
-          if (k <= p) acc[k] = fmaf((float)cs[k * (MMAX + 2) + i], v, acc[k]);
+          if (k <= p) acc[k] = fmaf(csf[k * (MMAX + 2) + i], v, acc[k]);
       }
 #pragma unroll
       for (int k = 0; k <= PP; ++k)
@@ -334,28 +343,32 @@ cudaError_t launch_combine(const void* V, int precision, long long N, const doub
 }
 
 // ---------------------------------------------------------------------------
-// lsa_arnoldi output: V[:, i] *= sigma_i for the stored columns 0..m_eff.
+// lsa_arnoldi output: copy the workspace basis into the caller's V, columns
+// 0..m_eff, scaled by the lazy scales sigma_i of the hybrid variants.
 
 template <class B>
-__global__ void k_scale_basis(B* V, long long N, int m, const Ctl* ctl) {
+__global__ void k_copy_basis(B* Vd, const B* Vs, long long N, int m, const Ctl* ctl, int apply_sigma) {
   const int me = __ldcg(&ctl->m_eff);
   const int cols = (me < m) ? me + 1 : m + 1;
   const long long total = N * cols;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += stride) {
-    int c = (int)(i / N);
-    double sc = __ldcg(&ctl->sigma[c]);
-    V[i] = (B)((double)V[i] * sc);
+    const int c = (int)(i / N);
+    B v = Vs[i];
+    if (apply_sigma) v = (B)((double)v * __ldcg(&ctl->sigma[c]));
+    Vd[i] = v;
   }
 }
 
-cudaError_t launch_scale_basis(void* V, int precision, long long N, int m, const Ctl* ctl,
-                               cudaStream_t s) {
+cudaError_t launch_copy_basis(void* Vd, const void* Vs, int precision, long long N, int m,
+                              const Ctl* ctl, int apply_sigma, cudaStream_t s) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (precision == LSA_FP64) k_scale_basis<double><<<sms * 8, 256, 0, s>>>((double*)V, N, m, ctl);
-  else k_scale_basis<float><<<sms * 8, 256, 0, s>>>((float*)V, N, m, ctl);
+  if (precision == LSA_FP64)
+    k_copy_basis<double><<<sms * 8, 256, 0, s>>>((double*)Vd, (const double*)Vs, N, m, ctl, apply_sigma);
+  else
+    k_copy_basis<float><<<sms * 8, 256, 0, s>>>((float*)Vd, (const float*)Vs, N, m, ctl, apply_sigma);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,45 @@
+"""The TMA-staged hybrid kernel (float32 basis, shapes that meet the TMA
+alignment rules) against the plain-load kernel and the oracle."""
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from tests.gpu_util import FP32_TOL, device_inputs, oracle_phiv, rel_errors
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+CASES = [W.adr3d(16, m=20, p=1), W.adr3d(48, m=40, p=1), W.advdiff2d(64, m=30, p=3),
+         W.advdiff2d(80, ny=48, m=24, p=2), W.grayscott2d(48, m=20, p=2, Du=2e-3, Dv=1e-3, h=0.5)]
+
+
+def run(cfg, variant, tma):
+    import paper_2410_14917_gb300 as lsa
+
+    old = os.environ.get("LSA_TMA")
+    os.environ["LSA_TMA"] = "1" if tma else "0"
+    try:
+        inp = W.make_inputs(cfg)
+        v, fields = device_inputs(cfg, inp, torch)
+        op = lsa.Operator.from_workload(cfg, fields)
+        y, st = lsa.phiv(op, v, cfg["h"], cfg["p"], cfg["m"], variant=variant, precision="fp32")
+        return y.cpu().numpy(), st
+    finally:
+        if old is None:
+            del os.environ["LSA_TMA"]
+        else:
+            os.environ["LSA_TMA"] = old
+
+
+@pytest.mark.parametrize("cfg", CASES, ids=[c["name"] for c in CASES])
+@pytest.mark.parametrize("variant", ["hcwy", "hncwy", "hgsmgs"])
+def test_tma_kernel_matches_plain_kernel_and_oracle(cfg, variant):
+    y_tma, st_tma = run(cfg, variant, True)
+    y_plain, st_plain = run(cfg, variant, False)
+    ref, _ = oracle_phiv(cfg)
+    assert max(rel_errors(y_tma, ref)) < FP32_TOL
+    assert max(rel_errors(y_plain, ref)) < FP32_TOL
+    assert max(rel_errors(y_tma, y_plain)) < FP32_TOL
+    assert st_tma["grid_syncs"] == st_plain["grid_syncs"] == cfg["m"] + 1 + st_tma["norm_fallbacks"]
