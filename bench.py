@@ -63,6 +63,21 @@ def dist_setup(args):
     return world, rank, local
 
 
+def aggregate_replicas(local_ms, steps, world, device=None):
+    """Whole-job throughput of independent replicas: every rank timed `steps`
+    phiv calls in `local_ms`; the job's time is the slowest rank's, and the
+    value counts all ranks' calls.  Returns (max_ms, calls per second)."""
+    t_ms = float(local_ms)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        t = torch.tensor([t_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+    return t_ms, world * steps / (t_ms / 1e3)
+
+
 def load_peaks():
     try:
         with open(PEAKS_PATH) as f:
@@ -287,11 +302,7 @@ def main():
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     tot_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([tot_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = world * args.steps / (tot_ms / 1e3)
+    tot_ms, value = aggregate_replicas(tot_ms, args.steps, world, dev)
 
     # end-to-end through the public API with host buffers: H2D of v, phiv, D2H of y
     y_host = torch.empty((p + 1, N), dtype=torch.float64).pin_memory()

@@ -33,17 +33,18 @@ namespace lsa {
 constexpr int TYH = TY + 2;   // rows of the tile-plus-y-halo box
 
 // Boxes over the extended basis tensor (x, y, zz, col); index q of each array
-// covers CBQ[q] = 8, 4, 2, 1 columns.
+// covers cbq(q) = 32, 16, 8, 4, 2, 1 columns.
+constexpr int NQ = 6;
 struct TmaMaps {
-  CUtensorMap mA[4];   // (TX, TY+2, NZB, cb): tile with both y-halo rows
-  CUtensorMap mB[4];   // (TX, TY, NZB, cb):   tile only
-  CUtensorMap mY[4];   // (TX, 1, NZB, cb):    one y-halo row
-  CUtensorMap mX[4];   // (16 bytes, TY, NZB, cb): x-halo column and its 16-byte neighbourhood
-  CUtensorMap mF0;     // operator field 0; box (TX, TY[, 1])
-  CUtensorMap mF1;     // operator field 1
+  CUtensorMap mA[NQ];   // (TX, TY+2, NZB, cb): tile with both y-halo rows
+  CUtensorMap mB[NQ];   // (TX, TY, NZB, cb):   tile only
+  CUtensorMap mY[NQ];   // (TX, 1, NZB, cb):    one y-halo row
+  CUtensorMap mX[NQ];   // (16 bytes, TY, NZB, cb): x-halo column and its 16-byte neighbourhood
+  CUtensorMap mF0;      // operator field 0; box (TX, TY[, 1])
+  CUtensorMap mF1;      // operator field 1
 };
 
-__host__ __device__ constexpr int cbq(int q) { return q == 0 ? 8 : (q == 1 ? 4 : (q == 2 ? 2 : 1)); }
+__host__ __device__ constexpr int cbq(int q) { return 32 >> q; }
 
 struct TmaParams {
   int ncap;          // bulk column slots per stage buffer (even)
@@ -218,9 +219,10 @@ struct TmaEngine {
     const int ylo = wrapi(T.y0 - 1, d.ny), yhi = wrapi(T.y0 + T.hg, d.ny);
     const int xl = wrapi(T.x0 - LY::XW, d.nx), xh = wrapi(T.x0 + T.w, d.nx);
     const int ncap = tp.ncap;
-    // column chunks of the bulk columns: 8, then 4, 2, 1 (the 1-chunk starts even)
-    const int n8 = ps.ncp >> 3, rem = ps.ncp & 7;
-    const int nch = n8 + ((rem >> 2) & 1) + ((rem >> 1) & 1) + (rem & 1);
+    // column chunks of the bulk columns: 32s, then 16, 8, 4, 2, 1 (odd-sized
+    // chunks start at even columns, which keeps every destination 128-byte aligned)
+    const int n32 = ps.ncp >> 5, rem = ps.ncp & 31;
+    const int nch = n32 + __popc(rem);
     // per chunk: tile box(es) and x-halo boxes; plus the same for the source column
     const int per = strips ? (full ? 3 : 5) : 1;
     const int nops = (nch + 1) * per;
@@ -236,15 +238,15 @@ struct TmaEngine {
     for (int o = e.lane; o < nops; o += 32) {
       const int ch = o / per, kind = o - ch * per;
       const bool src = ch == nch;
-      int q = 3, c0 = 0;
+      int q = NQ - 1, c0 = 0;
       if (!src) {
-        if (ch < n8) { q = 0; c0 = ch << 3; }
+        if (ch < n32) { q = 0; c0 = ch << 5; }
         else {
-          int k = ch - n8;          // k-th set bit of rem among 4, 2, 1
-          c0 = n8 << 3;
-          for (int b = 2; b >= 0; --b) {
+          int k = ch - n32;          // k-th set bit of rem among 16, 8, 4, 2, 1
+          c0 = n32 << 5;
+          for (int b = 4; b >= 0; --b) {
             if ((rem >> b) & 1) {
-              if (k == 0) { q = 2 - b + 1; break; }
+              if (k == 0) { q = 5 - b; break; }
               c0 += 1 << b;
               --k;
             }
@@ -708,7 +710,7 @@ cudaError_t launch_arnoldi_tma_op(const ArnoldiParams& P, int maxG, cudaStream_t
   const cuuint64_t strides[3] = {(cuuint64_t)d.nx * es, (cuuint64_t)d.nx * d.ny * es,
                                  (cuuint64_t)d.N * es};
   CUresult r = CUDA_SUCCESS;
-  for (int q = 0; q < 4 && r == CUDA_SUCCESS; ++q) {
+  for (int q = 0; q < NQ && r == CUDA_SUCCESS; ++q) {
     const cuuint32_t cb = (cuuint32_t)cbq(q);
     const cuuint32_t bA[4] = {TX, TYH, (cuuint32_t)LY::NZB, cb};
     const cuuint32_t bB[4] = {TX, TY, (cuuint32_t)LY::NZB, cb};
