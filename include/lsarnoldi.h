@@ -177,6 +177,76 @@ lsa_status lsa_phiv_noalloc(const lsa_op* op, const double* v, double h, int p, 
                             int variant, int precision, double* y, lsa_stats* stats,
                             void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Batched form: many independent phi products of one operator family (uneven
+ * grid sizes N_i and Krylov dimensions m_i) in one persistent launch.  Each
+ * instance is the computation of lsa_phiv; an exponential integrator needs
+ * one such Arnoldi projection per sub-step (Sect. 2.2, Eqs. 14-15), and many
+ * small ones do not fill the GPU one at a time.
+ *
+ * Packing: v holds v_0, v_1, ... back to back (instance i at element offset
+ * sum_{l<i} N_l); y holds the (p+1) x N_i outputs back to back (instance i at
+ * sum_{l<i} (p+1) N_l, row k at +k*N_i).  lsa_batch_info returns the offsets.
+ * All instances share h, p, tol, variant and precision; m_i is capped at N_i.
+ * Operator fields (field0/field1) must stay valid for the plan's lifetime.
+ *
+ * Tiling: the group_size CTAs of a group run one instance together (every
+ * barrier counted over the group); the nlarge costliest instances go to
+ * groups, the rest to single CTAs, each queue taken in order of decreasing
+ * cost.  group_size = lsa_batch_info's ctas with nlarge = count is one grid
+ * per instance; nlarge = 0 is one CTA per instance.  lsa_batch_tune times a
+ * set of tilings on the caller's data and keeps the fastest. */
+typedef struct lsa_batch lsa_batch;
+
+/* Device workspace bytes for a batch (0 if the arguments are invalid).
+ * ops, m: host arrays of `count` entries. */
+size_t lsa_batch_workspace_bytes(const lsa_op* ops, const int* m, int count, int p, int precision);
+
+/* Build a plan over a caller-provided workspace (256-byte aligned, at least
+ * lsa_batch_workspace_bytes).  Copies the instance table to the workspace
+ * (synchronising `stream`).  The plan owns host memory only; the workspace
+ * stays the caller's and must outlive the plan. */
+lsa_status lsa_batch_create(const lsa_op* ops, const int* m, int count, double h, int p,
+                            double tol, int variant, int precision, void* work, size_t work_bytes,
+                            lsa_batch** plan, void* stream);
+
+/* Plan facts: CTAs of the persistent launch, current tiling, packed sizes and
+ * (optional, `count` entries each) per-instance element offsets into v and y. */
+lsa_status lsa_batch_info(const lsa_batch* plan, int* ctas, int* group_size, int* nlarge,
+                          long long* v_elems, long long* y_elems, long long* voff, long long* yoff);
+
+/* Set the tiling: 1 <= group_size <= ctas, 0 <= nlarge <= count. */
+lsa_status lsa_batch_set_tiling(lsa_batch* plan, int group_size, int nlarge);
+
+/* Enqueue one batched evaluation on `stream` (two kernels: initialisation and
+ * the persistent kernel; nothing is read back).  use_graph != 0 captures the
+ * two launches once into a CUDA graph (on a private stream of the plan) and
+ * replays that graph on `stream`; the graph is rebuilt when v, y or the tiling
+ * change.  Per-instance results: lsa_batch_read_stats. */
+lsa_status lsa_batch_run(lsa_batch* plan, const double* v, double* y, int use_graph, void* stream);
+
+/* Synchronise `stream` and read the per-instance statistics of the last run
+ * into stats[0..count) (may be NULL) and the number of completed instances.
+ * Returns the first error of any instance (an instance that did not complete
+ * reports LSA_ERR_TIMEOUT), else the largest warning, else LSA_OK. */
+lsa_status lsa_batch_read_stats(const lsa_batch* plan, lsa_stats* stats, int* finished, void* stream);
+
+/* Time candidate tilings (one CTA per instance, one grid per instance, and
+ * groups of 2..32 CTAs for the costliest count/64 .. count/2 instances), each
+ * `reps` times after one warm-up run on the caller's v and y, keep the fastest
+ * and return it.  Synchronises `stream`; overwrites y. */
+lsa_status lsa_batch_tune(lsa_batch* plan, const double* v, double* y, int reps, int* group_size,
+                          int* nlarge, float* ms_best, void* stream);
+
+/* Release the plan's host memory and its graph (not the workspace). */
+void lsa_batch_destroy(lsa_batch* plan);
+
+/* One-shot batched call: create a plan with the default tiling, run it without
+ * a graph, read the statistics (stats: `count` entries or NULL), destroy it. */
+lsa_status lsa_phiv_batched(const lsa_op* ops, const int* m, int count, const double* v, double h,
+                            int p, double tol, int variant, int precision, double* y, void* work,
+                            size_t work_bytes, lsa_stats* stats, void* stream);
+
 /* Synchronise `stream` and read the statistics of the last call that used `work`. */
 lsa_status lsa_read_stats(const void* work, lsa_stats* out, void* stream);
 

@@ -20,7 +20,7 @@ from . import _binding as B
 from ._binding import LsaError, LsaOp, LsaStats, PRECISIONS, VARIANTS, KINDS
 
 __all__ = ["Operator", "phiv", "phiv_noalloc", "arnoldi", "matvec", "expm_phi", "workspace_bytes", "read_stats",
-           "selftest_barrier_timeout", "max_m", "LsaError", "Workspace"]
+           "selftest_barrier_timeout", "max_m", "LsaError", "Workspace", "Batch", "phiv_batched"]
 
 
 def _stream_ptr(stream):
@@ -203,3 +203,129 @@ def selftest_barrier_timeout(seconds: float = 0.5, stream=None) -> int:
     work = Workspace(1 << 16)
     return int(B.lib().lsa_selftest_barrier_timeout(ctypes.c_void_p(work.ptr), work.nbytes,
                                                     float(seconds), _stream_ptr(stream)))
+
+
+def _op_array(ops):
+    arr = (LsaOp * len(ops))()
+    for i, op in enumerate(ops):
+        arr[i] = op.c
+    return arr
+
+
+class Batch:
+    """A plan for many independent phi products in one persistent launch
+    (lsa_batch_* entry points).  Inputs and outputs are packed: v is the
+    concatenation of the N_i-vectors, y of the (p+1) x N_i outputs; `voff` and
+    `yoff` give each instance's element offset."""
+
+    def __init__(self, ops, m, h, p, tol=0.0, variant="hcwy", precision="fp64", stream=None):
+        self.ops = list(ops)               # keeps the operators' field tensors alive
+        self.count = len(self.ops)
+        self.p = int(p)
+        self._ops_c = _op_array(self.ops)
+        self._m_c = (ctypes.c_int * self.count)(*[int(x) for x in m])
+        nb = B.lib().lsa_batch_workspace_bytes(self._ops_c, self._m_c, self.count, self.p,
+                                               PRECISIONS[precision])
+        if nb == 0:
+            raise LsaError(B.LSA_ERR_ARG, "lsa_batch_workspace_bytes")
+        self.work = Workspace(nb)
+        h_ = ctypes.c_void_p()
+        st = B.lib().lsa_batch_create(self._ops_c, self._m_c, self.count, float(h), self.p,
+                                      float(tol), VARIANTS[variant], PRECISIONS[precision],
+                                      ctypes.c_void_p(self.work.ptr), self.work.nbytes,
+                                      ctypes.byref(h_), _stream_ptr(stream))
+        _check(st, "lsa_batch_create", ok=(B.LSA_OK,))
+        self._h = h_
+        ctas, gs, nl = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        nv, ny = ctypes.c_longlong(), ctypes.c_longlong()
+        vo = (ctypes.c_longlong * self.count)()
+        yo = (ctypes.c_longlong * self.count)()
+        _check(B.lib().lsa_batch_info(self._h, ctypes.byref(ctas), ctypes.byref(gs), ctypes.byref(nl),
+                                      ctypes.byref(nv), ctypes.byref(ny), vo, yo), "lsa_batch_info",
+               ok=(B.LSA_OK,))
+        self.ctas = ctas.value
+        self.v_elems, self.y_elems = nv.value, ny.value
+        self.voff, self.yoff = list(vo), list(yo)
+
+    @property
+    def tiling(self):
+        gs, nl = ctypes.c_int(), ctypes.c_int()
+        B.lib().lsa_batch_info(self._h, None, ctypes.byref(gs), ctypes.byref(nl), None, None, None, None)
+        return gs.value, nl.value
+
+    def set_tiling(self, group_size: int, nlarge: int):
+        _check(B.lib().lsa_batch_set_tiling(self._h, int(group_size), int(nlarge)),
+               "lsa_batch_set_tiling", ok=(B.LSA_OK,))
+
+    def _check_v(self, v, y):
+        if v.dtype != torch.float64 or not v.is_cuda or not v.is_contiguous() or v.numel() != self.v_elems:
+            raise ValueError("v must be a contiguous float64 CUDA tensor of the packed size")
+        if y is None:
+            y = torch.empty(self.y_elems, dtype=torch.float64, device=v.device)
+        elif y.dtype != torch.float64 or not y.is_contiguous() or y.numel() != self.y_elems:
+            raise ValueError("y must be a contiguous float64 CUDA tensor of the packed size")
+        return y
+
+    def run(self, v, y=None, graph=True, stream=None):
+        """Enqueue one evaluation (no synchronisation); returns y."""
+        y = self._check_v(v, y)
+        st = B.lib().lsa_batch_run(self._h, _ptr(v), _ptr(y), 1 if graph else 0, _stream_ptr(stream))
+        _check(st, "lsa_batch_run", ok=(B.LSA_OK,))
+        return y
+
+    def tune(self, v, y=None, reps=2, stream=None):
+        """Time candidate tilings on (v, y) and keep the fastest; returns
+        (group_size, nlarge, ms)."""
+        y = self._check_v(v, y)
+        gs, nl, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+        st = B.lib().lsa_batch_tune(self._h, _ptr(v), _ptr(y), int(reps), ctypes.byref(gs),
+                                    ctypes.byref(nl), ctypes.byref(ms), _stream_ptr(stream))
+        _check(st, "lsa_batch_tune")
+        return gs.value, nl.value, ms.value
+
+    def stats(self, stream=None):
+        """(status, finished, [per-instance stats dicts]) of the last run."""
+        arr = (LsaStats * self.count)()
+        fin = ctypes.c_int()
+        st = B.lib().lsa_batch_read_stats(self._h, arr, ctypes.byref(fin), _stream_ptr(stream))
+        return int(st), fin.value, [a.as_dict() for a in arr]
+
+    def split(self, y):
+        """Per-instance (p+1, N_i) views of a packed output."""
+        out = []
+        for i, op in enumerate(self.ops):
+            n = op.N
+            out.append(y[self.yoff[i]:self.yoff[i] + (self.p + 1) * n].view(self.p + 1, n))
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            B.lib().lsa_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def phiv_batched(ops, v, h, p, m, tol=0.0, variant="hcwy", precision="fp64", stream=None):
+    """One-shot batched call (lsa_phiv_batched, default tiling, no graph).
+    v packed as in Batch; returns (y packed, status, per-instance stats)."""
+    ops = list(ops)
+    n = len(ops)
+    ops_c = _op_array(ops)
+    m_c = (ctypes.c_int * n)(*[int(x) for x in m])
+    nb = B.lib().lsa_batch_workspace_bytes(ops_c, m_c, n, int(p), PRECISIONS[precision])
+    if nb == 0:
+        raise LsaError(B.LSA_ERR_ARG, "lsa_batch_workspace_bytes")
+    work = Workspace(nb)
+    ny = sum((int(p) + 1) * op.N for op in ops)
+    y = torch.empty(ny, dtype=torch.float64, device=v.device)
+    arr = (LsaStats * n)()
+    st = B.lib().lsa_phiv_batched(ops_c, m_c, n, _ptr(v), float(h), int(p), float(tol),
+                                  VARIANTS[variant], PRECISIONS[precision], _ptr(y),
+                                  ctypes.c_void_p(work.ptr), work.nbytes, arr, _stream_ptr(stream))
+    _check(st, "lsa_phiv_batched")
+    return y, int(st), [a.as_dict() for a in arr]

@@ -57,6 +57,21 @@ SIGNATURES = {
     "lsa_phiv_noalloc": (c_int, [POINTER(LsaOp), c_void_p, c_double, c_int, c_int, c_double, c_int,
                                  c_int, c_void_p, POINTER(LsaStats), c_void_p]),
     "lsa_selftest_barrier_timeout": (c_int, [c_void_p, c_size_t, c_double, c_void_p]),
+    "lsa_batch_workspace_bytes": (c_size_t, [POINTER(LsaOp), POINTER(c_int), c_int, c_int, c_int]),
+    "lsa_batch_create": (c_int, [POINTER(LsaOp), POINTER(c_int), c_int, c_double, c_int, c_double,
+                                 c_int, c_int, c_void_p, c_size_t, POINTER(c_void_p), c_void_p]),
+    "lsa_batch_info": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int),
+                               POINTER(c_longlong), POINTER(c_longlong), POINTER(c_longlong),
+                               POINTER(c_longlong)]),
+    "lsa_batch_set_tiling": (c_int, [c_void_p, c_int, c_int]),
+    "lsa_batch_run": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
+    "lsa_batch_read_stats": (c_int, [c_void_p, POINTER(LsaStats), POINTER(c_int), c_void_p]),
+    "lsa_batch_tune": (c_int, [c_void_p, c_void_p, c_void_p, c_int, POINTER(c_int), POINTER(c_int),
+                               POINTER(ctypes.c_float), c_void_p]),
+    "lsa_batch_destroy": (None, [c_void_p]),
+    "lsa_phiv_batched": (c_int, [POINTER(LsaOp), POINTER(c_int), c_int, c_void_p, c_double, c_int,
+                                 c_double, c_int, c_int, c_void_p, c_void_p, c_size_t,
+                                 POINTER(LsaStats), c_void_p]),
 }
 
 

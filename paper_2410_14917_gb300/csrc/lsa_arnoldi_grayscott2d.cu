@@ -1,5 +1,6 @@
 // Arnoldi kernels instantiated for the grayscott2d operator (one translation unit
 // per operator so that the library builds in parallel).
+#include "lsa_batched.cuh"
 #include "lsa_tma.cuh"
 
 namespace lsa {
@@ -20,5 +21,10 @@ cudaError_t launch_arnoldi_tma_grayscott2d(const ArnoldiParams& P, int precision
   return precision == LSA_FP32_BASIS ? launch_arnoldi_tma_op<OpGrayScott2D, float>(P, maxG, s)
                                      : launch_arnoldi_tma_op<OpGrayScott2D, double>(P, maxG, s);
 }
+
+cudaError_t launch_batched_grayscott2d(const BatchParams& BP, int precision, int G, cudaStream_t s) {
+  return launch_batched_op<OpGrayScott2D>(BP, precision, G, s);
+}
+int batched_blocks_per_sm_grayscott2d(int precision) { return batched_blocks_per_sm_op<OpGrayScott2D>(precision); }
 
 }  // namespace lsa

@@ -60,6 +60,7 @@ struct Engine {
   double* small;                     // MMAX x MMAX scratch of the last-arriving CTA
   Coef<Tc> cf;
   const int tid, lane, warp;
+  int grank, gsize;                  // this CTA's rank in its group and the group size
   __host__ __device__ static constexpr size_t small_offset() { return (sizeof(Smem) + 127) & ~(size_t)127; }
   __host__ __device__ static constexpr size_t smem_bytes() { return small_offset() + sizeof(double) * MMAX * MMAX; }
   // dot accumulators (per lane)
@@ -69,7 +70,8 @@ struct Engine {
   float fxx[2], fxw[2], fww[2];      // self terms (float32 form): Kahan sum, compensation
 
   __device__ Engine(const ArnoldiParams& p, Smem& s, double* sm)
-      : P(p), S(s), small(sm), tid(threadIdx.x), lane(threadIdx.x & 31), warp(threadIdx.x >> 5) {
+      : P(p), S(s), small(sm), tid(threadIdx.x), lane(threadIdx.x & 31), warp(threadIdx.x >> 5),
+        grank(blockIdx.x), gsize(gridDim.x) {
     cf.load(P.op);
   }
 
@@ -301,7 +303,7 @@ struct Engine {
     const Tiling& tl = P.tl;
     zero_acc();
     const bool stencil = ps.wout != nullptr;
-    for (int t = blockIdx.x; t < tl.ntiles; t += gridDim.x) {
+    for (int t = grank; t < tl.ntiles; t += gsize) {
       int bx = t % tl.tiles_x;
       int rr = t / tl.tiles_x;
       int by = rr % tl.tiles_y;
@@ -339,7 +341,7 @@ struct Engine {
   // Per-CTA partial sums of a pass to HBM (dot slots, then the three self terms).
   __device__ int write_partials(const PassT<B>& ps) {
     const int nd = ps.d1 > ps.d0 ? ps.d1 - ps.d0 : 0;
-    double* part = P.partials + (long long)blockIdx.x * SLOTS;
+    double* part = P.partials + (long long)grank * SLOTS;
 #pragma unroll
     for (int kk = 0; kk < KMAX; ++kk) {
       int c = ps.d0 + warp + NW * kk;
@@ -374,7 +376,7 @@ struct Engine {
   // loads are independent, so they are in flight together), then a fixed
   // butterfly combines the lanes: the result is deterministic for a given grid.
   __device__ void reduce_partials(int nslots) {
-    const int G = gridDim.x;
+    const int G = gsize;
     for (int s = warp; s < nslots; s += NW) {
       const double* ps = P.partials + s;
       double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
@@ -407,7 +409,7 @@ struct Engine {
   template <class Fn>
   __device__ bool reduce_step(unsigned& gen, int nslots, int ncoef_after, Fn fn) {
     const BarrierRef br = arnoldi_barrier(P.ctl);
-    int r = barrier_arrive(br, gen, gridDim.x, &S.flag, P.timeout_ns);
+    int r = barrier_arrive(br, gen, gsize, &S.flag, P.timeout_ns);
     if (r < 0) return false;
     if (r == 1) {
       reduce_partials(nslots);

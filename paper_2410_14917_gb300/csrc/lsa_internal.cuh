@@ -37,6 +37,7 @@ struct Ctl {
   int done;                // the Arnoldi loop has ended (breakdown)
   int fallback_pending;    // next pass is the explicit-norm fallback pass (Alg. 4)
   int expm_s;              // squarings used by the small exponential
+  int finished;            // batched form: the instance ran to its output
   double beta;
   double nrm_est;          // current norm estimate (hybrid)
   double a;                // scale of the source vector in the next projection

@@ -114,13 +114,14 @@ BATCH_SIDES = tuple(range(32, 257, 16))  # {32, 48, ..., 256}: 15 values
 
 
 def batched_advdiff2d(count=512, *, seed=SEED_BASE + 3, vel=(1.0, 0.5), h=1e-2, p=2,
-                      m_range=(16, 48), diff_range=(1e-4, 1e-1)):
+                      m_range=(16, 48), diff_range=(1e-4, 1e-1), sides=BATCH_SIDES):
     """Instance table of the batched workload: sides drawn uniformly from
     {32, 48, ..., 256}, diffusion log-uniform in [1e-4, 1e-1], m uniform in
     [16, 48].  Draw order from ``default_rng(seed)``: sides, diffusions, m's;
-    then each instance's v ~ U[-1,1]^(side^2) from ``default_rng(seed + 1 + i)``."""
+    then each instance's v ~ U[-1,1]^(side^2) from ``default_rng(seed + 1 + i)``.
+    ``sides`` replaces the side set (smaller test batches)."""
     rng = np.random.default_rng(seed)
-    sides = rng.choice(np.array(BATCH_SIDES), size=count)
+    sides = rng.choice(np.array(sides), size=count)
     lo, hi = math.log(diff_range[0]), math.log(diff_range[1])
     diffs = np.exp(rng.uniform(lo, hi, size=count))
     ms = rng.integers(m_range[0], m_range[1] + 1, size=count)
@@ -128,3 +129,8 @@ def batched_advdiff2d(count=512, *, seed=SEED_BASE + 3, vel=(1.0, 0.5), h=1e-2, 
                       name=f"batch{i}_{int(s)}")
             for i, (s, c, mm) in enumerate(zip(sides, diffs, ms))]
     return dict(name=f"batched_advdiff2d_{count}", kind="batched", instances=inst, h=h, p=p)
+
+
+def batched_inputs(bcfg: dict) -> list:
+    """Start vectors of every instance of a batched workload (in order)."""
+    return [make_inputs(c)["v"] for c in bcfg["instances"]]
