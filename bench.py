@@ -3,6 +3,9 @@
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--config I] [--variant hcwy] [--precision fp64]
 
+--config 3 selects the batched workload (512 advection-diffusion instances of
+uneven size in one persistent launch per step).
+
 A step is one phiv call -- the whole hot path (stencil matvecs, grouped
 reductions, correction, projection, small exponential, output combination) over
 one synthetic input.  Default workload: the Gray-Scott Jacobian on a 512x512
@@ -92,7 +95,7 @@ def workload(cfg_index, size=0):
 
     cfg = W.config(cfg_index)
     if cfg.get("kind") == "batched":
-        raise SystemExit("the batched workload is a parity case, not a bench line")
+        return cfg
     if size:
         ctor = {"advdiff2d": W.advdiff2d, "grayscott2d": W.grayscott2d, "adr3d": W.adr3d}[cfg["kind"]]
         cfg = ctor(size, h=cfg["h"], p=cfg["p"], m=cfg["m"], seed=cfg["seed"])
@@ -184,6 +187,9 @@ def run_reference(args, world, rank):
     from oracle import operators as OP
 
     cfg = workload(args.config, args.size)
+    if cfg.get("kind") == "batched":
+        run_reference_batched(args, world, cfg)
+        return
     inp = W.make_inputs(cfg)
     A = OP.from_workload(cfg, inp)
     variant = args.variant
@@ -213,6 +219,213 @@ def run_reference(args, world, rank):
             "e2e": {"value": value, "unit": "phiv/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def oracle_batch_sample(bcfg, variant, budget, max_calls=None):
+    """Time the oracle over the batch's instances in order until ~budget
+    seconds have passed (bounded sample).  Returns (calls, seconds, outputs)."""
+    import workloads as W
+    from oracle import krylov as OK
+    from oracle import operators as OP
+
+    t0 = time.perf_counter()
+    n = 0
+    outs = []
+    for c in bcfg["instances"]:
+        inp = W.make_inputs(c)
+        A = OP.from_workload(c, inp)
+        ts = time.perf_counter()
+        y, _ = OK.phiv(lambda x: A @ x, inp["v"], bcfg["h"], bcfg["p"], c["m"], variant)
+        outs.append(y)
+        n += 1
+        if time.perf_counter() - t0 > budget or (max_calls and n >= max_calls):
+            break
+    return n, time.perf_counter() - t0, outs
+
+
+def run_reference_batched(args, world, bcfg):
+    n, el, _ = oracle_batch_sample(bcfg, args.variant, 9 * args.cpu_budget,
+                                   max_calls=max(1, args.steps) * 8)
+    value = n / el
+    sample = (f"the first {n} of {len(bcfg['instances'])} instances of {bcfg['name']} "
+              f"({args.variant}, float64 NumPy/SciPy)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "phiv/s",
+            "n_gpus": world, "steps": n, "warmup": 0, "ms_per_step": 1e3 * el / n,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": bcfg["name"], "p": bcfg["p"],
+                                             "variant": args.variant, "precision": "fp64"},
+            "cpu_baseline": {"value": value, "unit": "phiv/s", "cores": os.cpu_count(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "phiv/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def bench_batched(args, world, rank, local, bcfg):
+    """The batched workload: all instances in one persistent launch (tuned
+    tiling, CUDA-graph replay) per step, beside a loop of single lsa_phiv
+    calls over the same instances."""
+    import numpy as np
+    import torch
+
+    import paper_2410_14917_gb300 as lsa
+    import workloads as W
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    insts = bcfg["instances"]
+    h, p = bcfg["h"], bcfg["p"]
+    ops = [lsa.Operator.from_workload(c, {}) for c in insts]
+    ms = [c["m"] for c in insts]
+    vs = W.batched_inputs(bcfg)
+    v_host = torch.from_numpy(np.concatenate(vs)).pin_memory()
+    v = v_host.to(dev)
+    b = lsa.Batch(ops, ms, h, p, variant=args.variant, precision=args.precision)
+    y = torch.empty(b.y_elems, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    flush = None if args.no_flush else torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    default_tiling = b.tiling
+    t_tune = time.perf_counter()
+    gs, nl, ms_tune = b.tune(v, y, reps=2)
+    t_tune = time.perf_counter() - t_tune
+    b.run(v, y, graph=True)
+    torch.cuda.synchronize()
+    st, fin, stats = b.stats()
+    if st < 0 or fin != b.count:
+        raise RuntimeError(f"batched run failed: status {st}, {fin}/{b.count} finished")
+    m_eff = [s["m_eff"] for s in stats]
+    for _ in range(args.warmup):
+        b.run(v, y, graph=True)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        if flush is not None:
+            flush.fill_(i & 0xFF)
+        ev[i][0].record(stream)
+        b.run(v, y, graph=True)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(c) for a, c in ev]
+    st, fin, _ = b.stats()
+    if st < 0 or fin != b.count:
+        raise RuntimeError(f"batched run failed: status {st}")
+    tot_ms, steps_per_s = aggregate_replicas(sum(step_ms), args.steps, world, dev)
+    value = steps_per_s * b.count
+
+    # a loop of single lsa_phiv calls over the same instances (one workspace)
+    big = max(range(len(ops)), key=lambda i: lsa.workspace_bytes(ops[i], ms[i], p, args.precision))
+    work = lsa.Workspace.for_call(ops[big], ms[big], p, args.precision)
+    parts = b.split(y)
+    ysingle = [torch.empty_like(t) for t in parts]
+    vparts = [v[b.voff[i]:b.voff[i] + ops[i].N] for i in range(b.count)]
+
+    def loop():
+        for i in range(b.count):
+            lsa.phiv(ops[i], vparts[i], h, p, ms[i], variant=args.variant, precision=args.precision,
+                     y=ysingle[i], work=work, stats=False)
+    loop()
+    torch.cuda.synchronize()
+    l0 = torch.cuda.Event(enable_timing=True)
+    l1 = torch.cuda.Event(enable_timing=True)
+    lsteps = 2
+    l0.record(stream)
+    for _ in range(lsteps):
+        loop()
+    l1.record(stream)
+    torch.cuda.synchronize()
+    loop_ms = l0.elapsed_time(l1) / lsteps
+    loop_diff = max(float((ysingle[i] - parts[i]).abs().max() / parts[i].abs().max().clamp_min(1e-300))
+                    for i in range(b.count))
+
+    # end to end with host buffers
+    y_host = torch.empty(b.y_elems, dtype=torch.float64).pin_memory()
+    e2e_steps = max(3, min(args.steps, 10))
+    vd = torch.empty_like(v)
+    b.run(vd, y, graph=True)           # capture once for the (vd, y) pair
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        vd.copy_(v_host, non_blocking=True)
+        b.run(vd, y, graph=True)
+        y_host.copy_(y, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_value = e2e_steps * b.count / (e0.elapsed_time(e1) / 1e3) * world
+
+    byts = flops = 0
+    for c, me in zip(insts, m_eff):
+        bb, ff = algorithmic_counts(c, args.precision, me)
+        byts += bb
+        flops += ff
+    ms_step = tot_ms / args.steps
+    hbm_peak, peak_kind = load_peaks()
+    gbs = byts / (ms_step / 1e3) / 1e9
+    if args.precision == "fp64":
+        achieved = flops / (ms_step / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "kernel": "k_batched (persistent batched phi products; step time incl. its init kernel)",
+                "peak_source": "FP64 FMA pipe from unit counts and max clock (152 SMs x 2 FMA/clk x 2.07 GHz)",
+                "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak, "algorithmic_bytes": byts,
+                "algorithmic_flops": flops}
+    else:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                "frac": gbs / hbm_peak, "traffic": None,
+                "kernel": "k_batched (persistent batched phi products; step time incl. its init kernel)",
+                "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes": byts,
+                "algorithmic_flops": flops}
+    line = {"metric": METRIC, "value": value, "unit": "phiv/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32-basis/f64", "data": "synthetic",
+            "config": {"workload": bcfg["name"], "instances": b.count, "p": p, "h": h,
+                       "variant": args.variant, "precision": args.precision,
+                       "N_total": int(b.v_elems), "ctas": b.ctas,
+                       "tiling": {"group_size": gs, "nlarge": nl, "tuned_ms": ms_tune,
+                                  "tune_s": t_tune, "default": list(default_tiling)},
+                       "graph": True,
+                       "l2": "flushed between timed steps (256 MiB write)" if flush is not None
+                       else "not flushed",
+                       "parallelism": f"replicas x{world}"},
+            "arnoldi_steps_per_s": steps_per_s * sum(m_eff),
+            "loop_of_single_calls": {"ms_per_batch": loop_ms, "phiv_per_s": b.count / (loop_ms / 1e3),
+                                     "speedup_of_batched": loop_ms / ms_step,
+                                     "max_rel_diff_vs_batched": loop_diff,
+                                     "launches_per_batch": 4 * b.count},
+            "roofline": roof,
+            "e2e": {"value": e2e_value, "unit": "phiv/s", "h2d_bytes_per_step": int(b.v_elems) * 8,
+                    "d2h_bytes_per_step": int(b.y_elems) * 8},
+            "gpu_launches": 2 * args.steps,
+            "clocks": clocks}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        n, el, outs = oracle_batch_sample(bcfg, "mgs", args.cpu_budget)
+        line["cpu_baseline"] = {"value": n / el, "unit": "phiv/s", "cores": os.cpu_count(),
+                                "kind": "oracle",
+                                "sample": f"the first {n} of {b.count} instances ({'mgs'}, float64 NumPy/SciPy)"}
+        errs = []
+        for i in range(n):
+            yi = parts[i].cpu().numpy()
+            errs.append(max(float(np.linalg.norm(yi[k] - outs[i][k]) / np.linalg.norm(outs[i][k]))
+                            for k in range(p + 1)))
+        line["rel_err_vs_oracle"] = max(errs)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    b.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
 
 
 def cpu_baseline(cfg, variant, budget):
@@ -250,9 +463,12 @@ def main():
     import paper_2410_14917_gb300 as lsa
     import workloads as W
 
+    cfg = workload(args.config, args.size)
+    if cfg.get("kind") == "batched":
+        bench_batched(args, world, rank, local, cfg)
+        return
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    cfg = workload(args.config, args.size)
     inp = W.make_inputs(cfg)
     N = W.n_dof(cfg)
     p, m, h = cfg["p"], cfg["m"], cfg["h"]
