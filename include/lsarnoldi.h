@@ -97,6 +97,8 @@ typedef struct {
   float ms_expm;          /* device time of the small exponential (phiv only) */
   float ms_combine;       /* device time of the output combination (phiv only) */
   int launches;           /* kernels this call launched */
+  int arnoldi_kernel;     /* Arnoldi kernel that ran: 0 plain loads, 1 TMA-staged tile+halo,
+                             2 streaming (interior-only TMA stages); filled by lsa_arnoldi/lsa_phiv */
 } lsa_stats;
 
 /* Largest supported Krylov dimension m. */

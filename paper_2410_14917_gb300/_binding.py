@@ -33,7 +33,7 @@ class LsaStats(ctypes.Structure):
                 ("norm_fallbacks", c_int), ("grid_syncs", c_int), ("grid_barriers", c_int),
                 ("beta", c_double), ("err_est", c_double), ("h_last", c_double),
                 ("ms_arnoldi", ctypes.c_float), ("ms_expm", ctypes.c_float),
-                ("ms_combine", ctypes.c_float), ("launches", c_int)]
+                ("ms_combine", ctypes.c_float), ("launches", c_int), ("arnoldi_kernel", c_int)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -23,6 +23,10 @@ bool tma_applicable_adr3d(const DevOp&, const Tiling&, int, int);
 cudaError_t launch_arnoldi_tma_advdiff2d(const ArnoldiParams&, int, int, cudaStream_t);
 cudaError_t launch_arnoldi_tma_grayscott2d(const ArnoldiParams&, int, int, cudaStream_t);
 cudaError_t launch_arnoldi_tma_adr3d(const ArnoldiParams&, int, int, cudaStream_t);
+bool stream_applicable_advdiff2d(const DevOp&, const Tiling&, int);
+bool stream_applicable_adr3d(const DevOp&, const Tiling&, int);
+cudaError_t launch_arnoldi_stream_advdiff2d(const ArnoldiParams&, cudaStream_t);
+cudaError_t launch_arnoldi_stream_adr3d(const ArnoldiParams&, cudaStream_t);
 
 static const long long kTimeoutNs = 5000000000LL;   // 5 s per barrier wait
 static const double kBreakdownTolFp64 = 1e-13;
@@ -130,7 +134,28 @@ static bool use_tma(const ArnoldiParams& P, int precision) {
   return tma_applicable_adr3d(P.op, P.tl, P.m, precision);
 }
 
+// The streaming kernel (interior-only TMA stages, halo by plain loads) runs
+// the hybrid variants of the float32-basis form for the single-species
+// operators whenever its stages fit (LSA_STREAM=0 in the environment disables
+// it; the other kernels then run).
+static bool use_stream(const ArnoldiParams& P, int precision) {
+  if (P.variant < LSA_HCWY || precision != LSA_FP32_BASIS || !P.E) return false;
+  const char* env = getenv("LSA_STREAM");
+  if (env && env[0] == '0') return false;
+  if (P.op.kind == LSA_OP_ADVDIFF2D) return stream_applicable_advdiff2d(P.op, P.tl, P.m);
+  if (P.op.kind == LSA_OP_ADR3D) return stream_applicable_adr3d(P.op, P.tl, P.m);
+  return false;
+}
+
+static int arnoldi_kernel_kind(const ArnoldiParams& P, int precision) {
+  return use_stream(P, precision) ? 2 : use_tma(P, precision) ? 1 : 0;
+}
+
 cudaError_t launch_arnoldi(const ArnoldiParams& P, int precision, int G, cudaStream_t s) {
+  if (use_stream(P, precision)) {
+    if (P.op.kind == LSA_OP_ADVDIFF2D) return launch_arnoldi_stream_advdiff2d(P, s);
+    return launch_arnoldi_stream_adr3d(P, s);
+  }
   if (use_tma(P, precision)) {
     const int maxG = sm_count() * 2;
     if (P.op.kind == LSA_OP_ADVDIFF2D) return launch_arnoldi_tma_advdiff2d(P, precision, maxG, s);
@@ -181,6 +206,11 @@ static bool make_layout(const DevOp& d, int m, int precision, Layout* L) {
   }
   L->g0 = take(nfield * sizeof(float));
   L->g1 = take(nfield * sizeof(float));
+  // edge array of the streaming kernel (single-species float32 operators on whole tiles)
+  const bool edges = precision == LSA_FP32_BASIS && d.ns == 1 && d.nx % TX == 0 && d.ny % TY == 0 &&
+                     (d.kind == LSA_OP_ADVDIFF2D || (d.kind == LSA_OP_ADR3D && d.nz % t.ZS == 0));
+  L->E = take(edges ? (size_t)(m + 3) * (size_t)(d.N / 8) * sizeof(float) : 0);
+  if (!edges) L->E = 0;
   L->total = off;
   L->G = G;
   return true;
@@ -205,6 +235,7 @@ static lsa_status fill_stats(const void* work, lsa_stats* out, cudaStream_t s) {
     out->h_last = c.h_last;
     out->ms_arnoldi = out->ms_expm = out->ms_combine = 0.f;
     out->launches = 0;
+    out->arnoldi_kernel = 0;
   }
   if (c.status < 0) return (lsa_status)c.status;
   if (c.breakdown) return LSA_BREAKDOWN;
@@ -267,6 +298,7 @@ static lsa_status prepare(const lsa_op* op, int m, int precision, void* work, si
   P.W0 = pr->w + pr->L.W0;
   P.W1 = pr->w + pr->L.W1;
   P.H = (double*)(pr->w + pr->L.H);
+  P.E = pr->L.E ? (float*)(pr->w + pr->L.E) : nullptr;
   P.m = m;
   P.brk_tol = precision == LSA_FP64 ? kBreakdownTolFp64 : kBreakdownTolFp32;
   P.timeout_ns = kTimeoutNs;
@@ -342,7 +374,7 @@ lsa_status lsa_arnoldi(const lsa_op* op, const double* v, int m, int variant, in
   P.write_vlast = 1;
   CallTimer tm(stats != nullptr, s);
   cudaError_t e = launch_init(P.ctl, pr.d, (float*)pr.d.g0, (float*)pr.d.g1, precision, H,
-                              (m + 1) * m, v, P.V, s);
+                              (m + 1) * m, v, P.V, s, use_stream(P, precision) ? P.E : nullptr);
   tm.mark(0);
   if (e == cudaSuccess) e = launch_arnoldi(P, precision, pr.L.G, s);
   tm.mark(1);
@@ -353,6 +385,7 @@ lsa_status lsa_arnoldi(const lsa_op* op, const double* v, int m, int variant, in
     lsa_status r = fill_stats(P.ctl, stats, s);
     stats->ms_arnoldi = tm.ms(0, 1);
     stats->launches = 3;
+    stats->arnoldi_kernel = arnoldi_kernel_kind(P, precision);
     return r;
   }
   return LSA_OK;
@@ -377,7 +410,7 @@ lsa_status lsa_phiv(const lsa_op* op, const double* v, double h, int p, int m, d
   P.write_vlast = 0;
   CallTimer tm(stats != nullptr, s);
   cudaError_t e = launch_init(P.ctl, pr.d, (float*)pr.d.g0, (float*)pr.d.g1, precision, P.H,
-                              (m + 1) * m, v, P.V, s);
+                              (m + 1) * m, v, P.V, s, use_stream(P, precision) ? P.E : nullptr);
   tm.mark(0);
   if (e == cudaSuccess) e = launch_arnoldi(P, precision, pr.L.G, s);
   tm.mark(1);
@@ -410,6 +443,7 @@ lsa_status lsa_phiv(const lsa_op* op, const double* v, double h, int p, int m, d
     stats->ms_expm = tm.ms(1, 2);
     stats->ms_combine = tm.ms(2, 3);
     stats->launches = 4;
+    stats->arnoldi_kernel = arnoldi_kernel_kind(P, precision);
     return r;
   }
   return LSA_OK;

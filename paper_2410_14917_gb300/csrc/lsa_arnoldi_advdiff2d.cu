@@ -1,6 +1,7 @@
 // Arnoldi kernels instantiated for the advdiff2d operator (one translation unit
 // per operator so that the library builds in parallel).
 #include "lsa_batched.cuh"
+#include "lsa_stream.cuh"
 #include "lsa_tma.cuh"
 
 namespace lsa {
@@ -20,6 +21,13 @@ bool tma_applicable_advdiff2d(const DevOp& d, const Tiling& tl, int m, int preci
 cudaError_t launch_arnoldi_tma_advdiff2d(const ArnoldiParams& P, int precision, int maxG, cudaStream_t s) {
   return precision == LSA_FP32_BASIS ? launch_arnoldi_tma_op<OpAdvDiff2D, float>(P, maxG, s)
                                      : launch_arnoldi_tma_op<OpAdvDiff2D, double>(P, maxG, s);
+}
+
+bool stream_applicable_advdiff2d(const DevOp& d, const Tiling& tl, int m) {
+  return stream_applicable_op<OpAdvDiff2D>(d, tl, m);
+}
+cudaError_t launch_arnoldi_stream_advdiff2d(const ArnoldiParams& P, cudaStream_t s) {
+  return launch_arnoldi_stream_op<OpAdvDiff2D>(P, s);
 }
 
 cudaError_t launch_batched_advdiff2d(const BatchParams& BP, int precision, int G, cudaStream_t s) {

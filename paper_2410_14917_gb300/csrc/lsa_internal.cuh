@@ -89,15 +89,25 @@ struct ArnoldiParams {
   int write_vlast;         // MGS/CGS2: write v_{m+1} (Arnoldi output only)
   double brk_tol;
   long long timeout_ns;
+  float* E;                // streaming float32 kernel: edge array, (m+3) columns of N/8 (or null)
 };
 
 // Workspace layout (all offsets 256-byte aligned).
 struct Layout {
-  size_t ctl, partials, T, L, H, V, W0, W1, small, coefs, g0, g1, total;
+  size_t ctl, partials, T, L, H, V, W0, W1, small, coefs, g0, g1, E, total;
   int G;                   // CTAs of the persistent Arnoldi kernel
 };
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Edge array of the streaming float32 kernel.  For every extended-basis
+// column and every TX x TY tile (bx, by) of plane z it holds the tile's
+// periodic x-halo: the TY values left of the tile (x = x0-1), then the TY
+// values right of it (x = x0+TX), 2*TY floats at edge_slot(); a column's
+// edges take N/8 floats.  Whoever writes a column also writes its edges.
+__host__ __device__ __forceinline__ long long edge_slot(int tiles_x, int tiles_y, int bx, int by, int z) {
+  return (((long long)z * tiles_y + by) * tiles_x + bx) * (2 * TY);
+}
 
 // Host helpers implemented in lsa_api.cu
 bool make_devop(const lsa_op* op, DevOp* d);
@@ -129,7 +139,8 @@ cudaError_t launch_expm(const SmallParams& P, cudaStream_t s);
 cudaError_t launch_combine(const void* V, int precision, long long N, const double* C, int ldc,
                            int p, const Ctl* ctl, double* y, cudaStream_t s);
 cudaError_t launch_init(Ctl* ctl, const DevOp& op, float* g0, float* g1, int precision,
-                        double* H, int ldh_total, const double* vin, void* vcol0, cudaStream_t s);
+                        double* H, int ldh_total, const double* vin, void* vcol0, cudaStream_t s,
+                        float* edge0 = nullptr);
 cudaError_t launch_copy_basis(void* Vdst, const void* Vsrc, int precision, long long N, int m,
                               const Ctl* ctl, int apply_sigma, cudaStream_t s);
 cudaError_t launch_timeout_selftest(Ctl* ctl, long long timeout_ns, cudaStream_t s);

@@ -2,7 +2,7 @@
 //
 // Each operator reads one grid point and its face neighbours from the
 // shared-memory planes of the projected vector (a TX x TY footprint plus a
-// one-point halo, row pitch PW) and returns A x at that point for every
+// one-point halo, row pitch RP, PW by default) and returns A x at that point for every
 // species.  The paper only needs the action v -> J v (Sect. 2.1); the three
 // operators are the synthetic stand-ins of the benchmark workloads.
 #pragma once
@@ -24,7 +24,7 @@ struct Coef {
 // 2D periodic advection-diffusion: A v = c Lap5 v - u.grad v (central).
 struct OpAdvDiff2D {
   static constexpr int NS = 1, DIM = 2, KIND = LSA_OP_ADVDIFF2D, NF = 0;
-  template <class Tc>
+  template <class Tc, int RP = PW>
   __device__ __forceinline__ static void apply_f(const Coef<Tc>& c, const Tc* zm, const Tc* z0,
                                                  const Tc* zp, int o, Tc, Tc, Tc* out) {
     (void)zm; (void)zp;
@@ -32,8 +32,8 @@ struct OpAdvDiff2D {
     Tc r = c.cC * x;
     r = fma(c.cW, z0[o - 1], r);
     r = fma(c.cE, z0[o + 1], r);
-    r = fma(c.cS, z0[o - PW], r);
-    r = fma(c.cN, z0[o + PW], r);
+    r = fma(c.cS, z0[o - RP], r);
+    r = fma(c.cN, z0[o + RP], r);
     out[0] = r;
   }
   template <class Tc>
@@ -49,7 +49,7 @@ struct OpAdvDiff2D {
 // float32 form.
 struct OpGrayScott2D {
   static constexpr int NS = 2, DIM = 2, KIND = LSA_OP_GRAYSCOTT2D, NF = 2;
-  template <class Tc>
+  template <class Tc, int RP = PW>
   __device__ __forceinline__ static void apply_f(const Coef<Tc>& c, const Tc* zm, const Tc* z0,
                                                  const Tc* zp, int o, Tc f0, Tc f1, Tc* out) {
     (void)zm; (void)zp;
@@ -59,8 +59,8 @@ struct OpGrayScott2D {
     const Tc* U = z0;
     const Tc* Vv = z0 + PS;
     Tc u = U[o], v = Vv[o];
-    Tc lu = (U[o - 1] + U[o + 1]) + (U[o - PW] + U[o + PW]) - (Tc)4 * u;
-    Tc lv = (Vv[o - 1] + Vv[o + 1]) + (Vv[o - PW] + Vv[o + PW]) - (Tc)4 * v;
+    Tc lu = (U[o - 1] + U[o + 1]) + (U[o - RP] + U[o + RP]) - (Tc)4 * u;
+    Tc lv = (Vv[o - 1] + Vv[o + 1]) + (Vv[o - RP] + Vv[o + RP]) - (Tc)4 * v;
     out[0] = c.du * lu - (a + c.F) * u - b * v;
     out[1] = c.dv * lv + (b - c.F - c.k) * v + a * u;
   }
@@ -78,15 +78,15 @@ struct OpGrayScott2D {
 // 3D periodic advection-diffusion-reaction with first-order upwinding.
 struct OpADR3D {
   static constexpr int NS = 1, DIM = 3, KIND = LSA_OP_ADR3D, NF = 1;
-  template <class Tc>
+  template <class Tc, int RP = PW>
   __device__ __forceinline__ static void apply_f(const Coef<Tc>& c, const Tc* zm, const Tc* z0,
                                                  const Tc* zp, int o, Tc rr, Tc, Tc* out) {
     Tc x = z0[o];
     Tc r = (c.cC + rr) * x;
     r = fma(c.cW, z0[o - 1], r);
     r = fma(c.cE, z0[o + 1], r);
-    r = fma(c.cS, z0[o - PW], r);
-    r = fma(c.cN, z0[o + PW], r);
+    r = fma(c.cS, z0[o - RP], r);
+    r = fma(c.cN, z0[o + RP], r);
     r = fma(c.cD, zm[o], r);
     r = fma(c.cU, zp[o], r);
     out[0] = r;

@@ -12,7 +12,7 @@ namespace lsa {
 // float copies of the coefficient fields used by the stencil.
 
 __global__ void k_init(Ctl* ctl, DevOp op, float* g0, float* g1, int precision, double* H,
-                       int hcount, const double* vin, void* vcol0) {
+                       int hcount, const double* vin, void* vcol0, float* edge0) {
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long stride = (long long)gridDim.x * blockDim.x;
   const int nctl = (int)(sizeof(Ctl) / sizeof(int));
@@ -23,6 +23,20 @@ __global__ void k_init(Ctl* ctl, DevOp op, float* g0, float* g1, int precision, 
       for (long long i = tid; i < op.N; i += stride) reinterpret_cast<double*>(vcol0)[i] = vin[i];
     else
       for (long long i = tid; i < op.N; i += stride) reinterpret_cast<float*>(vcol0)[i] = (float)vin[i];
+  }
+  if (vin && edge0) {   // x-halo edges of column 0 for the streaming kernel
+    const int tx = op.nx / TX, ty = op.ny / TY;
+    for (long long e = tid; e < op.N / 8; e += stride) {
+      const long long t = e / (2 * TY);
+      const int r = (int)(e - t * (2 * TY));
+      const int side = r / TY, ly = r - side * TY;
+      const int bx = (int)(t % tx);
+      const long long rest = t / tx;
+      const int by = (int)(rest % ty), z = (int)(rest / ty);
+      const int x = side ? (bx * TX + TX) % op.nx : (bx * TX - 1 + op.nx) % op.nx;
+      const int y = by * TY + ly;
+      edge0[e] = (float)vin[x + (long long)op.nx * (y + (long long)op.ny * z)];
+    }
   }
   if (precision == LSA_FP32_BASIS) {
     if (op.kind == LSA_OP_GRAYSCOTT2D) {
@@ -39,11 +53,11 @@ __global__ void k_init(Ctl* ctl, DevOp op, float* g0, float* g1, int precision, 
 }
 
 cudaError_t launch_init(Ctl* ctl, const DevOp& op, float* g0, float* g1, int precision, double* H,
-                        int hcount, const double* vin, void* vcol0, cudaStream_t s) {
+                        int hcount, const double* vin, void* vcol0, cudaStream_t s, float* edge0) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  k_init<<<sms * 4, 256, 0, s>>>(ctl, op, g0, g1, precision, H, hcount, vin, vcol0);
+  k_init<<<sms * 4, 256, 0, s>>>(ctl, op, g0, g1, precision, H, hcount, vin, vcol0, edge0);
   return cudaGetLastError();
 }
 

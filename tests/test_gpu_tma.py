@@ -18,8 +18,9 @@ CASES = [W.adr3d(16, m=20, p=1), W.adr3d(48, m=40, p=1), W.advdiff2d(64, m=30, p
 def run(cfg, variant, tma):
     import paper_2410_14917_gb300 as lsa
 
-    old = os.environ.get("LSA_TMA")
+    old = {k: os.environ.get(k) for k in ("LSA_TMA", "LSA_STREAM")}
     os.environ["LSA_TMA"] = "1" if tma else "0"
+    os.environ["LSA_STREAM"] = "0"
     try:
         inp = W.make_inputs(cfg)
         v, fields = device_inputs(cfg, inp, torch)
@@ -27,10 +28,11 @@ def run(cfg, variant, tma):
         y, st = lsa.phiv(op, v, cfg["h"], cfg["p"], cfg["m"], variant=variant, precision="fp32")
         return y.cpu().numpy(), st
     finally:
-        if old is None:
-            del os.environ["LSA_TMA"]
-        else:
-            os.environ["LSA_TMA"] = old
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
 
 
 @pytest.mark.parametrize("cfg", CASES, ids=[c["name"] for c in CASES])
@@ -42,4 +44,7 @@ def test_tma_kernel_matches_plain_kernel_and_oracle(cfg, variant):
     assert max(rel_errors(y_tma, ref)) < FP32_TOL
     assert max(rel_errors(y_plain, ref)) < FP32_TOL
     assert max(rel_errors(y_tma, y_plain)) < FP32_TOL
+    # the TMA-staged kernel needs rows of whole 16-byte units and ny >= TY + 2
+    staged = cfg["ny"] >= 18 and (cfg["nx"] * 4) % 16 == 0 and cfg["nx"] >= 16
+    assert st_tma["arnoldi_kernel"] == (1 if staged else 0) and st_plain["arnoldi_kernel"] == 0
     assert st_tma["grid_syncs"] == st_plain["grid_syncs"] == cfg["m"] + 1 + st_tma["norm_fallbacks"]
