@@ -107,7 +107,8 @@ struct StreamLayout {
   using E = Engine<Op, float, float>;
   static __host__ __device__ constexpr size_t ring_off() { return (sizeof(typename E::Smem) + 127) & ~(size_t)127; }
   static __host__ __device__ constexpr size_t bar_off() { return ring_off() + (size_t)SQ_NRING * SQ_RS * 4; }
-  static __host__ __device__ constexpr size_t stage_off() { return (bar_off() + 8 * SQ_NSTMAX + 127) & ~(size_t)127; }
+  static __host__ __device__ constexpr size_t tab_off() { return (bar_off() + 8 * SQ_NSTMAX + 15) & ~(size_t)15; }
+  static __host__ __device__ constexpr size_t stage_off() { return (tab_off() + 16 * 3 * NW * 2 + 127) & ~(size_t)127; }
 };
 
 template <class Op>
@@ -125,6 +126,7 @@ struct StreamEngine {
   unsigned fpar = 0;        // parity of the next wait, per stage
   unsigned pend = 0;        // thread 0: stages with copies not yet waited for
   int* s_stop;              // shared stop flag of this CTA
+  int4* itab;               // per pass: each warp's boxes per task kind (see build_issue_table)
 
   // per pass
   int n = 0, kn = 0, nst = 2, depth = 1, lag = 0, tpt = 1, ntask = 0, sbytes = 0;
@@ -134,8 +136,8 @@ struct StreamEngine {
   const int q, g, ly, lx4;
 
   __device__ StreamEngine(E& en, const StreamMaps& m, const StreamParams& p, float* rg,
-                          unsigned char* st, unsigned b, int* stop)
-      : e(en), maps(m), sp(p), ring(rg), stages(st), full0(b), s_stop(stop),
+                          unsigned char* st, unsigned b, int* stop, int4* tab)
+      : e(en), maps(m), sp(p), ring(rg), stages(st), full0(b), s_stop(stop), itab(tab),
         q(en.warp * 8 + (en.lane & 7)), g(en.lane >> 3), ly(q >> 2), lx4((q & 3) * 4) {}
 
   __device__ __forceinline__ const float* stage(int s) const {
@@ -237,49 +239,70 @@ struct StreamEngine {
     pend |= 1u << s;
   }
 
-  // The copies of task T into stage s.  The task's boxes form a list -- per
-  // map family the column ranges [0, 8a) and [8a, n) (when not empty) and the
-  // source, then the field -- and lane 0 of warp w issues boxes w, w+8, ...
-  __device__ __forceinline__ void issue(const STask& T, int s, const SPass& ps) {
+  // Per pass, lane 0 of every warp lists the boxes it issues for each kind of
+  // task (0: halo, y-halo not wrapping; 1: halo, wrapping; 2: no halo).  A
+  // task's boxes are -- per map family the column ranges [0, 8a) and [8a, n)
+  // (when not empty) and the source, then the field -- and warp w takes boxes
+  // w and w + 8.  Entry: (family | box index << 3, stage byte offset, column).
+  // Families: 0 tile + y-halo rows, 1 tile, 2 / 3 low / high y-halo row,
+  // 4 edge records, 5 field.
+  __device__ __forceinline__ void build_issue_table(const SPass& ps) {
     if (e.lane != 0) return;
+    const int a = n & ~7, b = n & 7;
+    const int per_fam = (a ? 1 : 0) + (b ? 1 : 0) + 1;
+    for (int kind = 0; kind < 3; ++kind) {
+      const bool halo = kind < 2, full = kind == 0;
+      const bool field = halo && NF > 0;
+      const int nfam = !halo ? 1 : (full ? 2 : 4);
+      const int nbox = nfam * per_fam + (field ? 1 : 0);
+      for (int slot = 0; slot < 2; ++slot) {
+        const int bi = e.warp + NW * slot;
+        int4 en = make_int4(-1, 0, 0, 0);
+        if (bi == nfam * per_fam && field) {
+          en = make_int4(5, offF() * 4, 0, 0);
+        } else if (bi < nbox) {
+          const int fam = bi / per_fam, r = bi - fam * per_fam;
+          const int rk = (a && r == 0) ? 0 : (b && r == (a ? 1 : 0)) ? 1 : 2;   // range, range, source
+          const int c0 = rk == 0 ? 0 : a;
+          const int col = rk == 2 ? ps.src_col : c0;
+          const int bidx = rk == 2 ? 0 : stream_box_index(rk == 0 ? a : b);
+          const int sl = rk == 2 ? n : c0;
+          const int fk = full ? (fam == 0 ? 0 : 4) : (!halo ? 1 : (fam == 0 ? 1 : fam == 3 ? 4 : fam + 1));
+          int dst;
+          if (fk == 0) dst = sl * SQ_COLH * 4;
+          else if (fk == 1) dst = sl * SQ_COL * 4;
+          else if (fk == 4) dst = (offE() + sl * SQ_EW) * 4;
+          else dst = (offY(fk - 2) + (rk == 2 ? stream_ysrc(n) : c0) * TX) * 4;
+          en = make_int4(fk | (bidx << 3), dst, col, 0);
+        }
+        itab[(kind * NW + e.warp) * 2 + slot] = en;
+      }
+    }
+  }
+
+  // The copies of task T into stage s (lane 0 of each warp, its table entries).
+  __device__ __forceinline__ void issue(const STask& T, int s) {
+    if (e.lane != 0) return;
+    const bool halo = has_halo(T), full = is_full(T);
+    const int kind = full ? 0 : (halo ? 1 : 2);
     const unsigned bar = full0 + 8u * s;
     const unsigned base = smem_u32(stages) + (unsigned)(s * sbytes);
     const DevOp& d = e.P.op;
-    const Tiling& tl = e.P.tl;
     const int zz = (DIM == 3) ? wrapi(T.z, d.nz) : 0;
     const int x0 = T.bx * TX, y0 = T.by * TY;
-    const bool halo = has_halo(T), full = is_full(T);
-    const bool field = halo && NF > 0;
-    const int a = n & ~7, b = n & 7;
-    // families: full tile {A, E}; wrapping tile {I, Y-, Y+, E}; no halo {I}
-    const int nfam = !halo ? 1 : (full ? 2 : 4);
-    const int per_fam = (a ? 1 : 0) + (b ? 1 : 0) + 1;
-    const int nbox = nfam * per_fam + (field ? 1 : 0);
-    for (int bi = e.warp; bi < nbox; bi += NW) {
-      if (bi == nfam * per_fam) {
-        tma_load_3d(base + (unsigned)(offF() * 4), &maps.mF, x0, y0, zz, bar);
-        continue;
-      }
-      const int fam = bi / per_fam, r = bi - fam * per_fam;
-      // box r of a family: range [0, a) (if a), range [a, n) (if b), the source
-      const int kind = (a && r == 0) ? 0 : (b && r == (a ? 1 : 0)) ? 1 : 2;
-      const int c0 = kind == 0 ? 0 : a;
-      const int col = kind == 2 ? ps.src_col : c0;
-      const int bidx = kind == 2 ? 0 : stream_box_index(kind == 0 ? a : b);
-      const int slot = kind == 2 ? n : c0;
-      const int fk = full ? (fam == 0 ? 0 : 3) : (!halo ? 1 : (fam == 0 ? 1 : fam == 3 ? 3 : 2));
-      if (fk == 0) {                                    // tile and both y-halo rows
-        tma_load_4d(base + (unsigned)(slot * SQ_COLH * 4), &maps.mA[bidx], x0, y0 - 1, zz, col, bar);
-      } else if (fk == 1) {                             // tile only
-        tma_load_4d(base + (unsigned)(slot * SQ_COL * 4), &maps.mI[bidx], x0, y0, zz, col, bar);
-      } else if (fk == 2) {                             // one y-halo row (wrapping tile)
-        const int side = fam - 1;
-        const int ys = kind == 2 ? stream_ysrc(n) : c0;
-        tma_load_4d(base + (unsigned)((offY(side) + ys * TX) * 4), &maps.mY[bidx], x0,
-                    side ? wrapi(y0 + TY, d.ny) : wrapi(y0 - 1, d.ny), zz, col, bar);
-      } else {                                          // edge records
-        tma_load_4d(base + (unsigned)((offE() + slot * SQ_EW) * 4), &maps.mE[bidx], 0, T.bx,
-                    T.by + tl.tiles_y * zz, col, bar);
+#pragma unroll
+    for (int slot = 0; slot < 2; ++slot) {
+      const int4 en = itab[(kind * NW + e.warp) * 2 + slot];
+      if (en.x < 0) break;
+      const int fk = en.x & 7, bidx = en.x >> 3;
+      const unsigned dst = base + (unsigned)en.y;
+      switch (fk) {
+        case 0: tma_load_4d(dst, &maps.mA[bidx], x0, y0 - 1, zz, en.z, bar); break;
+        case 1: tma_load_4d(dst, &maps.mI[bidx], x0, y0, zz, en.z, bar); break;
+        case 2: tma_load_4d(dst, &maps.mY[bidx], x0, wrapi(y0 - 1, d.ny), zz, en.z, bar); break;
+        case 3: tma_load_4d(dst, &maps.mY[bidx], x0, wrapi(y0 + TY, d.ny), zz, en.z, bar); break;
+        case 4: tma_load_4d(dst, &maps.mE[bidx], 0, T.bx, T.by + e.P.tl.tiles_y * zz, en.z, bar); break;
+        default: tma_load_3d(dst, &maps.mF, x0, y0, zz, bar); break;
       }
     }
   }
@@ -343,19 +366,24 @@ struct StreamEngine {
 
   // x (quad) = a*src - sum_c coef_c V_c over this thread's KN column slots;
   // `p` points at slot 0 of the quad, `cs` is the slot stride.
-  template <int KN>
-  __device__ __forceinline__ float4 proj_quad(const float* p, int cs, float a) const {
-    const float* coef = e.S.coefc;
+  // x (quad) = a*src - sum_c coef_c V_c over this thread's KN column slots;
+  // `p` points at slot 0 of the quad, CS is the slot stride.  Slots below
+  // KN-1 are always columns (4(KN-1) + 3 < n + 3); the last one may be past n
+  // and then reads the source slot with a zero coefficient.
+  template <int KN, int CS>
+  __device__ __forceinline__ float4 proj_quad(const float* p, float a) const {
+    const float* coef = e.S.coefc + g;
+    const float* pg = p + g * CS;
     float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
     if (g == 0) {
-      const float4 sv = lds4(p + n * cs);
+      const float4 sv = lds4(p + n * CS);
       x = make_float4(a * sv.x, a * sv.y, a * sv.z, a * sv.w);
     }
 #pragma unroll
     for (int k = 0; k < KN; ++k) {
-      const int c = g + SQ_NG * k;
-      const float4 v = lds4(p + min(c, n) * cs);
-      const float cc = coef[c];
+      const float* pk = (k + 1 < KN || g + SQ_NG * k < n) ? pg + SQ_NG * k * CS : p + n * CS;
+      const float4 v = lds4(pk);
+      const float cc = coef[SQ_NG * k];
       x.x = fmaf(-cc, v.x, x.x);
       x.y = fmaf(-cc, v.y, x.y);
       x.z = fmaf(-cc, v.z, x.z);
@@ -363,24 +391,26 @@ struct StreamEngine {
     }
     return x;
   }
-  template <int KN>
-  __device__ __forceinline__ float proj_point(const float* p, int cs, int sslot, float a) const {
-    const float* coef = e.S.coefc;
-    float x = (g == 0) ? a * p[sslot * cs] : 0.f;
+  template <int KN, int CS>
+  __device__ __forceinline__ float proj_point(const float* p, int sslot, float a) const {
+    const float* coef = e.S.coefc + g;
+    const float* pg = p + g * CS;
+    float x = (g == 0) ? a * p[sslot * CS] : 0.f;
 #pragma unroll
     for (int k = 0; k < KN; ++k) {
-      const int c = g + SQ_NG * k;
-      x = fmaf(-coef[c], p[(c < n ? c : sslot) * cs], x);
+      const float* pk = (k + 1 < KN || g + SQ_NG * k < n) ? pg + SQ_NG * k * CS : p + sslot * CS;
+      x = fmaf(-coef[SQ_NG * k], *pk, x);
     }
     return x;
   }
-  template <int KN>
-  __device__ __forceinline__ void dots_quad(const float* p, int cs, const float4& x4, const float4& w4,
+  template <int KN, int CS>
+  __device__ __forceinline__ void dots_quad(const float* p, const float4& x4, const float4& w4,
                                             StreamAcc<SQ_KC>& A) const {
+    const float* pg = p + g * CS;
 #pragma unroll
     for (int k = 0; k < KN; ++k) {
-      const int c = g + SQ_NG * k;
-      const float4 v = lds4(p + min(c, n) * cs);
+      const float* pk = (k + 1 < KN || g + SQ_NG * k < n) ? pg + SQ_NG * k * CS : p + n * CS;
+      const float4 v = lds4(pk);
       float px = v.x * x4.x, pw = v.x * w4.x;
       px = fmaf(v.y, x4.y, px);
       pw = fmaf(v.y, w4.y, pw);
@@ -393,31 +423,34 @@ struct StreamEngine {
     }
   }
 
-  // Per-column-count dispatch of the inner loops (kn = ceil(n/4) slots per thread).
+  // Per-column-count (and stride) dispatch of the inner loops (kn = ceil(n/4)).
 #define LSA_SQ_CASES(X) X(0) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15)
-  __device__ __forceinline__ float4 proj_quad_n(const float* p, int cs, float a) const {
+  template <int CS>
+  __device__ __forceinline__ float4 proj_quad_n(const float* p, float a) const {
     switch (kn) {
-#define LSA_SQ_C(K) case K: return proj_quad<K>(p, cs, a);
+#define LSA_SQ_C(K) case K: return proj_quad<K, CS>(p, a);
       LSA_SQ_CASES(LSA_SQ_C)
 #undef LSA_SQ_C
-      default: return proj_quad<16>(p, cs, a);
+      default: return proj_quad<16, CS>(p, a);
     }
   }
-  __device__ __forceinline__ float proj_point_n(const float* p, int cs, int sslot, float a) const {
+  template <int CS>
+  __device__ __forceinline__ float proj_point_n(const float* p, int sslot, float a) const {
     switch (kn) {
-#define LSA_SQ_C(K) case K: return proj_point<K>(p, cs, sslot, a);
+#define LSA_SQ_C(K) case K: return proj_point<K, CS>(p, sslot, a);
       LSA_SQ_CASES(LSA_SQ_C)
 #undef LSA_SQ_C
-      default: return proj_point<16>(p, cs, sslot, a);
+      default: return proj_point<16, CS>(p, sslot, a);
     }
   }
-  __device__ __forceinline__ void dots_quad_n(const float* p, int cs, const float4& x4, const float4& w4,
+  template <int CS>
+  __device__ __forceinline__ void dots_quad_n(const float* p, const float4& x4, const float4& w4,
                                               StreamAcc<SQ_KC>& A) const {
     switch (kn) {
-#define LSA_SQ_C(K) case K: dots_quad<K>(p, cs, x4, w4, A); return;
+#define LSA_SQ_C(K) case K: dots_quad<K, CS>(p, x4, w4, A); return;
       LSA_SQ_CASES(LSA_SQ_C)
 #undef LSA_SQ_C
-      default: dots_quad<16>(p, cs, x4, w4, A); return;
+      default: dots_quad<16, CS>(p, x4, w4, A); return;
     }
   }
 #undef LSA_SQ_CASES
@@ -428,8 +461,8 @@ struct StreamEngine {
     const float* st = stage(s);
     const float a = (float)ps.a;
     const bool full = is_full(T);
-    const int cs = full ? SQ_COLH : SQ_COL;
-    const float4 x = proj_quad_n(st + (ly + (full ? 1 : 0)) * TX + lx4, cs, a);
+    const float4 x = full ? proj_quad_n<SQ_COLH>(st + (ly + 1) * TX + lx4, a)
+                          : proj_quad_n<SQ_COL>(st + ly * TX + lx4, a);
     const float xg = pick(make_float4(bfly(x.x), bfly(x.y), bfly(x.z), bfly(x.w)), g);
     float* rg = ring + rs * SQ_RS;
     rg[(ly + 1) * SQ_RP + 4 + lx4 + g] = xg;
@@ -443,10 +476,10 @@ struct StreamEngine {
       float hx;
       if (q < 2 * TX) {                    // y-halo rows
         const int side = q >= TX ? 1 : 0, hx0 = q & (TX - 1);
-        if (full) hx = proj_point_n(st + side * (TY + 1) * TX + hx0, SQ_COLH, n, a);
-        else hx = proj_point_n(st + offY(side) + hx0, TX, stream_ysrc(n), a);
+        if (full) hx = proj_point_n<SQ_COLH>(st + side * (TY + 1) * TX + hx0, n, a);
+        else hx = proj_point_n<TX>(st + offY(side) + hx0, stream_ysrc(n), a);
       } else {                             // x-halo from the edge records
-        hx = proj_point_n(st + offE() + (q - 2 * TX), SQ_EW, n, a);
+        hx = proj_point_n<SQ_EW>(st + offE() + (q - 2 * TX), n, a);
       }
       hx = bfly(hx);
       if (g == 0) rg[halo_ring(q)] = hx;
@@ -480,7 +513,8 @@ struct StreamEngine {
     w4.w = __shfl_sync(0xffffffffu, w, src + 24);
     const float4 x4 = lds4(x0 + (ly + 1) * SQ_RP + 4 + lx4);
     const bool full = is_full(Td);
-    dots_quad_n(sd + (ly + (full ? 1 : 0)) * TX + lx4, full ? SQ_COLH : SQ_COL, x4, w4, A);
+    if (full) dots_quad_n<SQ_COLH>(sd + (ly + 1) * TX + lx4, x4, w4, A);
+    else dots_quad_n<SQ_COL>(sd + ly * TX + lx4, x4, w4, A);
   }
 
   // The task loop of a pass and its per-CTA partial sums (x dots, w dots,
@@ -505,7 +539,7 @@ struct StreamEngine {
       __syncthreads();
       if (ld_volatile_i32(s_stop)) break;
       // the stage of task i-1-lag is free: refill it with task i+depth
-      if (refill) issue(Ti, si, ps);
+      if (refill) issue(Ti, si);
       bool compute = stencil;
       if (DIM == 3 && stencil) compute = cur.k >= 2;   // the stencil of plane z-1 needs plane z
       if (compute) {
@@ -591,12 +625,13 @@ struct StreamEngine {
         cursor_next(c);
       }
     }
+    build_issue_table(ps);
     __syncthreads();
     if (e.lane == 0) {
       asm volatile("fence.proxy.async;" ::: "memory");   // and global writes before the TMA reads
       Cursor c = cursor_at(0);
       for (int t = 0; t < depth && t < ntask; ++t) {
-        issue(task_of(c), t, ps);
+        issue(task_of(c), t);
         cursor_next(c);
       }
     }
@@ -669,7 +704,7 @@ __global__ void __launch_bounds__(NT, 1)
   }
   __syncthreads();
   StreamEngine<Op> t(e, maps, sp, reinterpret_cast<float*>(smem_raw + LY::ring_off()), stages, bar0,
-                     &S.stop);
+                     &S.stop, reinterpret_cast<int4*>(smem_raw + LY::tab_off()));
   t.run_hybrid();
 }
 
