@@ -15,6 +15,7 @@ import scipy.linalg
 import scipy.sparse.linalg
 
 import workloads as W
+from oracle import adjoint as OAD
 from oracle import arnoldi as OA
 from oracle import exact as OE
 from oracle import expm as OX
@@ -332,3 +333,47 @@ def pin_sync_counts():
         expect = [1 + (1 if j == m else 0) for j in range(1, m + 1)]
         bad += sum((s - f) != e for s, e, f in zip(r["syncs"], expect, [0] * m)) if r["fallbacks"] == 0 else 0
     return float(bad)
+
+
+# --- adjoint (gradients of 1/2 ||phi_1(hA(theta))v - y_t||^2) ----------------
+
+def _adjoint_case(n=4, Du=0.05, Dv=0.03, h=0.7, seed=7):
+    cfg = W.grayscott2d(n, Du=Du, Dv=Dv, h=h, p=1, m=2 * 2 * n * n, seed=seed)
+    inp = W.adjoint_inputs(cfg)
+    A, dA = OAD.grayscott_parts(cfg, inp)
+    return cfg, inp, A, dA
+
+
+def pin_adjoint_vs_dense():
+    """Krylov gradients (m = full dimension) against dense exponentials and
+    scipy's Frechet derivative of exp on the Eq. 7 matrix (tiny grid)."""
+    cfg, inp, A, dA = _adjoint_case()
+    gk = OAD.grads_krylov(A, dA, inp["v"], inp["y_target"], cfg["h"], cfg["m"])
+    gd = OAD.grads_dense(A, dA, inp["v"], inp["y_target"], cfg["h"])
+    rel = lambda a, b: float(np.max(np.abs(np.asarray(a) - np.asarray(b))) / np.max(np.abs(b)))
+    return max(abs(gk["L"] - gd["L"]) / gd["L"], rel(gk["dv"], gd["dv"]), abs(gk["dh"] - gd["dh"]) / abs(gd["dh"]),
+               rel(gk["dtheta"], gd["dtheta"]))
+
+
+def pin_adjoint_finite_differences(n=8, eps=1e-6, m=60):
+    """Krylov gradients against central differences of the loss (step eps) in
+    v (a random direction), h and each theta_k."""
+    cfg, inp, A, dA = _adjoint_case(n=n, seed=11)
+    v, yt, h = inp["v"], inp["y_target"], cfg["h"]
+    g = OAD.grads_krylov(A, dA, v, yt, h, m)
+    th = np.array([cfg["diff"], cfg["diff2"], cfg["F"], cfg["k"]])
+
+    def L_at(theta=th, vv=v, hh=h):
+        At, _ = OAD.grayscott_parts(cfg, inp, theta)
+        return OAD.loss(At, vv, yt, hh, m)[0]
+
+    d = np.random.default_rng(3).standard_normal(v.size)
+    d /= np.linalg.norm(d)
+    errs = [abs((L_at(vv=v + eps * d) - L_at(vv=v - eps * d)) / (2 * eps) - g["dv"] @ d) / np.linalg.norm(g["dv"]),
+            abs((L_at(hh=h + eps) - L_at(hh=h - eps)) / (2 * eps) - g["dh"]) / abs(g["dh"])]
+    for k in range(4):
+        e = np.zeros(4)
+        e[k] = eps
+        fd = (L_at(theta=th + e) - L_at(theta=th - e)) / (2 * eps)
+        errs.append(abs(fd - g["dtheta"][k]) / max(abs(g["dtheta"][k]), 1e-12))
+    return max(errs)

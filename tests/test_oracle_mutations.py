@@ -85,3 +85,30 @@ def test_grayscott_coupling_slip_is_caught(monkeypatch):
         return sp.bmat([[Du * lap - a - F * I, b], [a, Dv * lap + b - (F + k) * I]], format="csr")
     monkeypatch.setattr(OP, "grayscott2d", bad)
     assert pins.pin_grayscott_jacobian() > 1e-3
+
+
+def test_adjoint_transpose_slip_is_caught(monkeypatch):
+    from oracle import adjoint as OAD
+    orig = OAD.grads_krylov
+
+    def bad(A, dA, v, y_t, h, m, variant="mgs"):
+        g = orig(A, dA, v, y_t, h, m, variant)
+        y, _ = OK.phiv(lambda x: A @ x, g["r"], h, 1, m, variant)    # A instead of A^T
+        g["dv"] = y[1]
+        return g
+    monkeypatch.setattr(OAD, "grads_krylov", bad)
+    assert pins.pin_adjoint_finite_differences() > 1e-3
+
+
+def test_adjoint_derivative_sign_slip_is_caught(monkeypatch):
+    from oracle import adjoint as OAD
+    orig = OAD.grayscott_parts
+
+    def bad(cfg, inp, theta=None):
+        A, dA = orig(cfg, inp, theta)
+        dA[2] = -dA[2]                                                # dA/dF = +I
+        return A, dA
+    monkeypatch.setattr(OAD, "grayscott_parts", bad)
+    # the dense reference shares dA with the Krylov gradients: the central
+    # differences of the loss are the pin that sees this slip
+    assert pins.pin_adjoint_finite_differences() > 1e-3

@@ -107,6 +107,20 @@ def make_inputs(cfg: dict) -> dict:
     return out
 
 
+def adjoint_inputs(cfg: dict) -> dict:
+    """Inputs of the adjoint workload (a Gray-Scott configuration): those of
+    ``make_inputs`` followed, from the same generator, by the target
+    y_t ~ U[-1,1]^N of the loss 1/2 ||phi_1(hA)v - y_t||^2."""
+    if cfg["kind"] != GRAYSCOTT2D:
+        raise ValueError("the adjoint workload is a Gray-Scott configuration")
+    rng = np.random.default_rng(cfg["seed"])
+    npts = cfg["nx"] * cfg["ny"]
+    out = {"u0": rng.uniform(0.0, 1.0, npts), "v0": rng.uniform(0.0, 1.0, npts)}
+    out["v"] = rng.uniform(-1.0, 1.0, 2 * npts)
+    out["y_target"] = rng.uniform(-1.0, 1.0, 2 * npts)
+    return out
+
+
 # ---------------------------------------------------------------------------
 # Batched workload: 512 independent 2D advection-diffusion instances.
 
