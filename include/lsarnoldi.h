@@ -60,7 +60,13 @@ typedef enum { LSA_MGS = 0, LSA_CGS2 = 1, LSA_HCWY = 2, LSA_HNCWY = 3, LSA_HGSMG
  * estimate and the small exponential stay in double. */
 typedef enum { LSA_FP64 = 0, LSA_FP32_BASIS = 1 } lsa_precision;
 
-typedef enum { LSA_OP_ADVDIFF2D = 1, LSA_OP_GRAYSCOTT2D = 2, LSA_OP_ADR3D = 3 } lsa_op_kind;
+typedef enum {
+  LSA_OP_ADVDIFF2D = 1,
+  LSA_OP_GRAYSCOTT2D = 2,
+  LSA_OP_ADR3D = 3,
+  LSA_OP_GRAYSCOTT2D_T = 4,        /* LSA_FP64 only */
+  LSA_OP_GRAYSCOTT2D_FRECHET = 5   /* LSA_FP64 only */
+} lsa_op_kind;
 
 /* Operator descriptor (plain data; the library only borrows the field pointers).
  *  LSA_OP_ADVDIFF2D  periodic nx*ny grid:  A v = diff*Lap5 v - vel[0]*Dx v - vel[1]*Dy v,
@@ -70,6 +76,16 @@ typedef enum { LSA_OP_ADVDIFF2D = 1, LSA_OP_GRAYSCOTT2D = 2, LSA_OP_ADR3D = 3 } 
  *                    nz must be 1, N = 2*nx*ny.
  *  LSA_OP_ADR3D      periodic nx*ny*nz grid: A v = diff*Lap7 v - sum_a vel[a]*Upwind_a v + r.*v,
  *                    r = field0 (N values), first-order upwind differences.
+ *  LSA_OP_GRAYSCOTT2D_T  the transpose A^T of the Gray-Scott Jacobian (same fields):
+ *                    [[diff*Lap - v0^2 - F, v0^2], [-2 u0 v0, diff2*Lap + 2 u0 v0 - (F+k)]].
+ *  LSA_OP_GRAYSCOTT2D_FRECHET  the block operator K = [[A, dA/dtheta], [0, A]] of the
+ *                    Gray-Scott Jacobian A (same fields) on [a; b], N = 4*nx*ny (four
+ *                    species blocks a_u, a_v, b_u, b_v), theta = (diff, diff2, F, k)[aux]:
+ *                    dA/ddiff = [[Lap, 0], [0, 0]], dA/ddiff2 = [[0, 0], [0, Lap]],
+ *                    dA/dF = -I, dA/dk = [[0, 0], [0, -I]].  The top half of
+ *                    phi_1(hK)[0; v] is the derivative of phi_1(hA)v along h*dA/dtheta
+ *                    (Sect. 2.1, Eq. 7 with the block-triangular augmentation of the
+ *                    Frechet derivative of exp).
  * All operators use the uniform spacing dx in every direction. */
 typedef struct {
   int kind;
@@ -81,6 +97,7 @@ typedef struct {
   double F, k;
   const double* field0;   /* dev, see above; NULL when unused */
   const double* field1;   /* dev, see above; NULL when unused */
+  int aux;                /* LSA_OP_GRAYSCOTT2D_FRECHET: derivative direction 0..3; else 0 */
 } lsa_op;
 
 typedef struct {
@@ -178,6 +195,31 @@ lsa_status lsa_expm_phi(const double* H, int ldh, int m, double h, int p, double
 lsa_status lsa_phiv_noalloc(const lsa_op* op, const double* v, double h, int p, int m, double tol,
                             int variant, int precision, double* y, lsa_stats* stats,
                             void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Gradients of a loss L(y) of the phi_1 product y = phi_1(h A(theta)) v on the
+ * Gray-Scott Jacobian (LSA_OP_GRAYSCOTT2D), theta = (diff, diff2, F, k), given
+ * r = dL/dy -- the vector-Jacobian product behind an autograd function:
+ *   dL/dv     = phi_1(h A^T) r                       (phi_1(hA)^T = phi_1(hA^T), Eq. 6)
+ *   dL/dh     = r . (phi_0(hA)v - phi_1(hA)v) / h    (d/dh [h phi_1(hA)] = e^{hA})
+ *   dL/dtheta = r . [phi_1(hK)[0; v]]_top, K = [[A, dA/dtheta], [0, A]]
+ *               (LSA_OP_GRAYSCOTT2D_FRECHET: the block-triangular augmentation of
+ *               the Frechet derivative of exp applied to Sect. 2.1's Eq. 7 matrix).
+ * Six phi products with m Krylov steps each, all float64: one on A^T (N) and
+ * four on K (2N); no Krylov basis is kept between calls (each is rebuilt).
+ *  op        LSA_OP_GRAYSCOTT2D descriptor of A(theta) (aux ignored).
+ *  v, r      dev, N doubles.    y  dev, 2 x N doubles: phi_0(hA)v then phi_1(hA)v
+ *            (lsa_phiv with p = 1 and the same h, m and variant).
+ *  h         finite and nonzero.   m, variant as lsa_phiv.
+ *  grad_v    dev, N doubles (output).
+ *  grad_s    dev, 5 doubles (output): dL/dh, dL/ddiff, dL/ddiff2, dL/dF, dL/dk.
+ *  work      dev workspace of lsa_phiv_vjp_workspace_bytes(op, m), 256-byte aligned.
+ * stats as lsa_phiv (when non-NULL: the calls synchronise, the worst status of
+ * the six products is returned and their counters are summed). */
+size_t lsa_phiv_vjp_workspace_bytes(const lsa_op* op, int m);
+lsa_status lsa_phiv_vjp(const lsa_op* op, const double* v, double h, int m, int variant,
+                        const double* r, const double* y, double* grad_v, double* grad_s,
+                        void* work, size_t work_bytes, lsa_stats* stats, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Batched form: many independent phi products of one operator family (uneven

@@ -20,7 +20,8 @@ from . import _binding as B
 from ._binding import LsaError, LsaOp, LsaStats, PRECISIONS, VARIANTS, KINDS
 
 __all__ = ["Operator", "phiv", "phiv_noalloc", "arnoldi", "matvec", "expm_phi", "workspace_bytes", "read_stats",
-           "selftest_barrier_timeout", "max_m", "LsaError", "Workspace", "Batch", "phiv_batched"]
+           "selftest_barrier_timeout", "max_m", "LsaError", "Workspace", "Batch", "phiv_batched",
+           "phiv_vjp", "Phi1GrayScott"]
 
 
 def _stream_ptr(stream):
@@ -37,8 +38,10 @@ class Operator:
     """Operator descriptor; keeps the device field tensors alive."""
 
     def __init__(self, kind, nx, ny, nz, dx, diff=0.0, diff2=0.0, vel=(0.0, 0.0, 0.0), F=0.0,
-                 k=0.0, field0=None, field1=None):
+                 k=0.0, field0=None, field1=None, aux=0):
         self.kind = kind
+        self.args = dict(nx=nx, ny=ny, nz=nz, dx=dx, diff=diff, diff2=diff2, vel=vel, F=F, k=k,
+                         field0=field0, field1=field1, aux=aux)
         self.fields = [f for f in (field0, field1) if f is not None]
         for f in self.fields:
             if f.dtype != torch.float64 or not f.is_cuda or not f.is_contiguous():
@@ -47,7 +50,14 @@ class Operator:
         self.c = LsaOp(KINDS[kind], int(nx), int(ny), int(nz), float(dx), float(diff),
                        float(diff2), (ctypes.c_double * 3)(*v), float(F), float(k),
                        ctypes.c_void_p(field0.data_ptr() if field0 is not None else None),
-                       ctypes.c_void_p(field1.data_ptr() if field1 is not None else None))
+                       ctypes.c_void_p(field1.data_ptr() if field1 is not None else None), int(aux))
+
+    def derived(self, kind=None, aux=0, **changes):
+        """A descriptor of another kind (e.g. the transpose) or with changed
+        coefficients, sharing the field tensors."""
+        args = dict(self.args, aux=aux)
+        args.update(changes)
+        return Operator(kind or self.kind, **args)
 
     @property
     def N(self) -> int:
@@ -329,3 +339,67 @@ def phiv_batched(ops, v, h, p, m, tol=0.0, variant="hcwy", precision="fp64", str
                                   ctypes.c_void_p(work.ptr), work.nbytes, arr, _stream_ptr(stream))
     _check(st, "lsa_phiv_batched")
     return y, int(st), [a.as_dict() for a in arr]
+
+
+# ---------------------------------------------------------------------------
+# Gradients of the phi_1 product on the Gray-Scott Jacobian
+
+def vjp_workspace_bytes(op: Operator, m: int) -> int:
+    n = B.lib().lsa_phiv_vjp_workspace_bytes(ctypes.byref(op.c), int(m))
+    if n == 0:
+        raise LsaError(B.LSA_ERR_ARG, "lsa_phiv_vjp_workspace_bytes")
+    return int(n)
+
+
+def phiv_vjp(op: Operator, v: torch.Tensor, h: float, m: int, r: torch.Tensor, y: torch.Tensor,
+             variant="hcwy", work=None, stream=None, stats=False):
+    """Vector-Jacobian product of y1 = phi_1(h A(theta)) v (Gray-Scott, float64)
+    for the cotangent r: returns (dL/dv, tensor of dL/dh, dL/dDu, dL/dDv, dL/dF,
+    dL/dk on the device, stats or None).  y is the (2, N) output of
+    phiv(op, v, h, p=1, m) -- phi_0 and phi_1 products."""
+    N = v.numel()
+    for t, name in ((v, "v"), (r, "r"), (y, "y")):
+        if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous float64 CUDA tensor")
+    if r.numel() != N or y.numel() != 2 * N:
+        raise ValueError("r must have N elements and y 2N")
+    grad_v = torch.empty_like(v)
+    grad_s = torch.empty(5, dtype=torch.float64, device=v.device)
+    work = work or Workspace(vjp_workspace_bytes(op, m), device=v.device)
+    s = LsaStats()
+    st = B.lib().lsa_phiv_vjp(ctypes.byref(op.c), _ptr(v), float(h), int(m), VARIANTS[variant], _ptr(r),
+                              _ptr(y), _ptr(grad_v), _ptr(grad_s), ctypes.c_void_p(work.ptr), work.nbytes,
+                              ctypes.byref(s) if stats else None, _stream_ptr(stream))
+    _check(st, "lsa_phiv_vjp")
+    return grad_v, grad_s, (s.as_dict() if stats else None)
+
+
+class Phi1GrayScott(torch.autograd.Function):
+    """y = phi_1(h A(theta)) v for the Gray-Scott Jacobian A(theta), theta =
+    (Du, Dv, F, k), differentiable in v (CUDA float64), h and theta (CPU
+    float64 tensors).  The forward keeps v, h, theta and the phi_0 / phi_1
+    products; the backward recomputes every Krylov basis it needs through
+    lsa_phiv_vjp (no basis is stored).
+
+        y = Phi1GrayScott.apply(v, h, theta, op, m, variant)
+
+    op supplies the grid, spacing and fields (its own coefficients are replaced
+    by theta)."""
+
+    @staticmethod
+    def forward(ctx, v, h, theta, op, m, variant="hcwy"):
+        hh = float(h)
+        Du, Dv, F, k = (float(t) for t in theta)
+        opt = op.derived(kind="grayscott2d", diff=Du, diff2=Dv, F=F, k=k)
+        y, _ = phiv(opt, v.contiguous(), hh, 1, m, variant=variant, stats=False)
+        ctx.save_for_backward(v, y)
+        ctx.opt, ctx.h, ctx.m, ctx.variant = opt, hh, m, variant
+        ctx.theta_dev = theta.device
+        return y[1].clone()
+
+    @staticmethod
+    def backward(ctx, g):
+        v, y = ctx.saved_tensors
+        gv, gs, _ = phiv_vjp(ctx.opt, v, ctx.h, ctx.m, g.contiguous(), y, variant=ctx.variant)
+        gs = gs.to(ctx.theta_dev)
+        return gv, gs[0], gs[1:5], None, None, None

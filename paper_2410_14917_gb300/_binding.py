@@ -18,14 +18,14 @@ LSA_ERR_ARG, LSA_ERR_CUDA, LSA_ERR_TIMEOUT, LSA_ERR_NUMERIC, LSA_ERR_WORKSPACE =
 
 VARIANTS = {"mgs": 0, "cgs2": 1, "hcwy": 2, "hncwy": 3, "hgsmgs": 4}
 PRECISIONS = {"fp64": 0, "fp32": 1}
-KINDS = {"advdiff2d": 1, "grayscott2d": 2, "adr3d": 3}
+KINDS = {"advdiff2d": 1, "grayscott2d": 2, "adr3d": 3, "grayscott2d_t": 4, "grayscott2d_frechet": 5}
 
 
 class LsaOp(ctypes.Structure):
     _fields_ = [("kind", c_int), ("nx", c_int), ("ny", c_int), ("nz", c_int),
                 ("dx", c_double), ("diff", c_double), ("diff2", c_double),
                 ("vel", c_double * 3), ("F", c_double), ("k", c_double),
-                ("field0", c_void_p), ("field1", c_void_p)]
+                ("field0", c_void_p), ("field1", c_void_p), ("aux", c_int)]
 
 
 class LsaStats(ctypes.Structure):
@@ -69,6 +69,9 @@ SIGNATURES = {
     "lsa_batch_tune": (c_int, [c_void_p, c_void_p, c_void_p, c_int, POINTER(c_int), POINTER(c_int),
                                POINTER(ctypes.c_float), c_void_p]),
     "lsa_batch_destroy": (None, [c_void_p]),
+    "lsa_phiv_vjp_workspace_bytes": (c_size_t, [POINTER(LsaOp), c_int]),
+    "lsa_phiv_vjp": (c_int, [POINTER(LsaOp), c_void_p, c_double, c_int, c_int, c_void_p, c_void_p,
+                             c_void_p, c_void_p, c_void_p, c_size_t, POINTER(LsaStats), c_void_p]),
     "lsa_phiv_batched": (c_int, [POINTER(LsaOp), POINTER(c_int), c_int, c_void_p, c_double, c_int,
                                  c_double, c_int, c_int, c_void_p, c_void_p, c_size_t,
                                  POINTER(LsaStats), c_void_p]),

@@ -28,6 +28,13 @@ bool stream_applicable_adr3d(const DevOp&, const Tiling&, int);
 cudaError_t launch_arnoldi_stream_advdiff2d(const ArnoldiParams&, cudaStream_t);
 cudaError_t launch_arnoldi_stream_adr3d(const ArnoldiParams&, cudaStream_t);
 
+cudaError_t launch_arnoldi_grayscott2d_t(const ArnoldiParams&, int, int, cudaStream_t);
+cudaError_t launch_matvec_grayscott2d_t(const ArnoldiParams&, int, const void*, void*, int, cudaStream_t);
+int blocks_per_sm_grayscott2d_t(int);
+cudaError_t launch_arnoldi_grayscott2d_frechet(const ArnoldiParams&, int, int, cudaStream_t);
+cudaError_t launch_matvec_grayscott2d_frechet(const ArnoldiParams&, int, const void*, void*, int, cudaStream_t);
+int blocks_per_sm_grayscott2d_frechet(int);
+
 static const long long kTimeoutNs = 5000000000LL;   // 5 s per barrier wait
 static const double kBreakdownTolFp64 = 1e-13;
 static const double kBreakdownTolFp32 = 1e-6;
@@ -55,12 +62,17 @@ bool make_devop(const lsa_op* op, DevOp* d) {
       d->cC = -4.0 * op->diff * inv;
       break;
     case LSA_OP_GRAYSCOTT2D:
+    case LSA_OP_GRAYSCOTT2D_T:
+    case LSA_OP_GRAYSCOTT2D_FRECHET:
       if (op->nz != 1 || !op->field0 || !op->field1) return false;
-      d->ns = 2;
+      if (op->kind == LSA_OP_GRAYSCOTT2D_FRECHET && (op->aux < 0 || op->aux > 3)) return false;
+      d->ns = op->kind == LSA_OP_GRAYSCOTT2D_FRECHET ? 4 : 2;
       d->du = op->diff * inv;
       d->dv = op->diff2 * inv;
       d->F = op->F;
       d->k = op->k;
+      d->idx2 = inv;
+      d->dir = op->kind == LSA_OP_GRAYSCOTT2D_FRECHET ? op->aux : 0;
       d->f0 = op->field0;
       d->f1 = op->field1;
       break;
@@ -106,7 +118,7 @@ static int sm_count() {
 }
 
 int arnoldi_blocks_per_sm(const DevOp& d, int precision) {
-  static int cache[4][2][16];
+  static int cache[6][2][16];
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 16) dev = 0;
@@ -115,6 +127,8 @@ int arnoldi_blocks_per_sm(const DevOp& d, int precision) {
   int nb = 0;
   if (d.kind == LSA_OP_ADVDIFF2D) nb = blocks_per_sm_advdiff2d(precision);
   else if (d.kind == LSA_OP_GRAYSCOTT2D) nb = blocks_per_sm_grayscott2d(precision);
+  else if (d.kind == LSA_OP_GRAYSCOTT2D_T) nb = blocks_per_sm_grayscott2d_t(precision);
+  else if (d.kind == LSA_OP_GRAYSCOTT2D_FRECHET) nb = blocks_per_sm_grayscott2d_frechet(precision);
   else nb = blocks_per_sm_adr3d(precision);
   c = nb;
   return nb;
@@ -125,7 +139,7 @@ int arnoldi_blocks_per_sm(const DevOp& d, int precision) {
 // alignment rules (LSA_TMA=0 in the environment disables it, LSA_TMA=1 also
 // allows it for the float64 form).
 static bool use_tma(const ArnoldiParams& P, int precision) {
-  if (P.variant < LSA_HCWY) return false;
+  if (P.variant < LSA_HCWY || P.op.kind > LSA_OP_ADR3D) return false;
   const char* env = getenv("LSA_TMA");
   if (env && env[0] == '0') return false;
   if (precision == LSA_FP64 && !(env && env[0] == '1')) return false;
@@ -164,6 +178,8 @@ cudaError_t launch_arnoldi(const ArnoldiParams& P, int precision, int G, cudaStr
   }
   if (P.op.kind == LSA_OP_ADVDIFF2D) return launch_arnoldi_advdiff2d(P, precision, G, s);
   if (P.op.kind == LSA_OP_GRAYSCOTT2D) return launch_arnoldi_grayscott2d(P, precision, G, s);
+  if (P.op.kind == LSA_OP_GRAYSCOTT2D_T) return launch_arnoldi_grayscott2d_t(P, precision, G, s);
+  if (P.op.kind == LSA_OP_GRAYSCOTT2D_FRECHET) return launch_arnoldi_grayscott2d_frechet(P, precision, G, s);
   return launch_arnoldi_adr3d(P, precision, G, s);
 }
 
@@ -171,6 +187,9 @@ cudaError_t launch_matvec(const ArnoldiParams& P, int precision, const void* x, 
                           cudaStream_t s) {
   if (P.op.kind == LSA_OP_ADVDIFF2D) return launch_matvec_advdiff2d(P, precision, x, y, G, s);
   if (P.op.kind == LSA_OP_GRAYSCOTT2D) return launch_matvec_grayscott2d(P, precision, x, y, G, s);
+  if (P.op.kind == LSA_OP_GRAYSCOTT2D_T) return launch_matvec_grayscott2d_t(P, precision, x, y, G, s);
+  if (P.op.kind == LSA_OP_GRAYSCOTT2D_FRECHET)
+    return launch_matvec_grayscott2d_frechet(P, precision, x, y, G, s);
   return launch_matvec_adr3d(P, precision, x, y, G, s);
 }
 
@@ -278,6 +297,7 @@ static lsa_status prepare(const lsa_op* op, int m, int precision, void* work, si
                           Prepared* pr) {
   if (precision != LSA_FP64 && precision != LSA_FP32_BASIS) return LSA_ERR_ARG;
   if (!make_devop(op, &pr->d)) return LSA_ERR_ARG;
+  if (pr->d.kind > LSA_OP_ADR3D && precision != LSA_FP64) return LSA_ERR_ARG;
   if (m < 1 || m > MMAX) return LSA_ERR_ARG;
   if (!make_layout(pr->d, m, precision, &pr->L)) return LSA_ERR_CUDA;
   if (!work || !aligned256(work) || work_bytes < pr->L.total) return LSA_ERR_WORKSPACE;
@@ -338,6 +358,7 @@ size_t lsa_workspace_bytes(const lsa_op* op, int m, int p, int precision) {
   DevOp d;
   if (precision != LSA_FP64 && precision != LSA_FP32_BASIS) return 0;
   if (!make_devop(op, &d) || m < 1 || m > MMAX || p < 0 || p > PMAX) return 0;
+  if (d.kind > LSA_OP_ADR3D && precision != LSA_FP64) return 0;
   Layout L;
   if (!make_layout(d, m, precision, &L)) return 0;
   return L.total;

@@ -92,6 +92,7 @@ static lsa_status batch_layout(const lsa_op* ops, const int* ms, int count, int 
   BL->m.resize(count);
   for (int i = 0; i < count; ++i) {
     if (!make_devop(&ops[i], &BL->d[i])) return LSA_ERR_ARG;
+    if (BL->d[i].kind > LSA_OP_ADR3D) return LSA_ERR_ARG;     // the three workload operators
     if (BL->d[i].kind != BL->d[0].kind) return LSA_ERR_ARG;   // one operator family per batch
     if (ms[i] < 1 || ms[i] > MMAX) return LSA_ERR_ARG;
     BL->m[i] = (long long)ms[i] > BL->d[i].N ? (int)BL->d[i].N : ms[i];

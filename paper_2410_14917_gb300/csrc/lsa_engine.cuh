@@ -854,59 +854,52 @@ __global__ void __launch_bounds__(NT) k_matvec(ArnoldiParams P, const B* x, B* y
   e.run_pass(ps);
 }
 
-template <class Op>
-cudaError_t launch_arnoldi_op(const ArnoldiParams& P, int precision, int G, cudaStream_t s) {
+template <class Op, class Tc>
+cudaError_t launch_arnoldi_t(const ArnoldiParams& P, int G, cudaStream_t s) {
   ArnoldiParams Pc = P;
   void* args[1] = {&Pc};
-  if (precision == LSA_FP64) {
-    auto k = k_arnoldi<Op, double, double>;
-    size_t sm = Engine<Op, double, double>::smem_bytes();
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    return cudaLaunchCooperativeKernel((void*)k, dim3(G), dim3(NT), args, sm, s);
-  } else {
-    auto k = k_arnoldi<Op, float, float>;
-    size_t sm = Engine<Op, float, float>::smem_bytes();
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    return cudaLaunchCooperativeKernel((void*)k, dim3(G), dim3(NT), args, sm, s);
-  }
+  auto k = k_arnoldi<Op, Tc, Tc>;
+  size_t sm = Engine<Op, Tc, Tc>::smem_bytes();
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  return cudaLaunchCooperativeKernel((void*)k, dim3(G), dim3(NT), args, sm, s);
+}
+
+template <class Op, class Tc>
+cudaError_t launch_matvec_t(const ArnoldiParams& P, const void* x, void* y, int G, cudaStream_t s) {
+  auto k = k_matvec<Op, Tc, Tc>;
+  size_t sm = Engine<Op, Tc, Tc>::smem_bytes();
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k<<<G, NT, sm, s>>>(P, (const Tc*)x, (Tc*)y);
+  return cudaGetLastError();
+}
+
+template <class Op, class Tc>
+int blocks_per_sm_t() {
+  int nb = 0;
+  auto k = k_arnoldi<Op, Tc, Tc>;
+  size_t sm = Engine<Op, Tc, Tc>::smem_bytes();
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, NT, sm);
+  return nb;
+}
+
+template <class Op>
+cudaError_t launch_arnoldi_op(const ArnoldiParams& P, int precision, int G, cudaStream_t s) {
+  return precision == LSA_FP64 ? launch_arnoldi_t<Op, double>(P, G, s) : launch_arnoldi_t<Op, float>(P, G, s);
 }
 
 template <class Op>
 cudaError_t launch_matvec_op(const ArnoldiParams& P, int precision, const void* x, void* y, int G,
                              cudaStream_t s) {
-  if (precision == LSA_FP64) {
-    auto k = k_matvec<Op, double, double>;
-    size_t sm = Engine<Op, double, double>::smem_bytes();
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    k<<<G, NT, sm, s>>>(P, (const double*)x, (double*)y);
-  } else {
-    auto k = k_matvec<Op, float, float>;
-    size_t sm = Engine<Op, float, float>::smem_bytes();
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    k<<<G, NT, sm, s>>>(P, (const float*)x, (float*)y);
-  }
-  return cudaGetLastError();
+  return precision == LSA_FP64 ? launch_matvec_t<Op, double>(P, x, y, G, s)
+                               : launch_matvec_t<Op, float>(P, x, y, G, s);
 }
 
 template <class Op>
 int blocks_per_sm_op(int precision) {
-  int nb = 0;
-  if (precision == LSA_FP64) {
-    auto k = k_arnoldi<Op, double, double>;
-    size_t sm = Engine<Op, double, double>::smem_bytes();
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, NT, sm);
-  } else {
-    auto k = k_arnoldi<Op, float, float>;
-    size_t sm = Engine<Op, float, float>::smem_bytes();
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, NT, sm);
-  }
-  return nb;
+  return precision == LSA_FP64 ? blocks_per_sm_t<Op, double>() : blocks_per_sm_t<Op, float>();
 }
 
 }  // namespace lsa

@@ -59,8 +59,10 @@ struct DevOp {
   long long N;             // ns*npts
   // advdiff2d / adr3d: folded neighbour coefficients; center excludes r
   double cW, cE, cS, cN, cD, cU, cC;
-  // grayscott2d
+  // grayscott2d (and its transpose and Frechet block operator)
   double du, dv, F, k;     // du = Du/dx^2, dv = Dv/dx^2
+  double idx2;             // 1/dx^2
+  int dir;                 // Frechet block operator: derivative direction 0..3 = Du, Dv, F, k
   const double* f0;        // fp64 fields (u0 / r)
   const double* f1;        // fp64 field v0
   const float* g0;         // fp32 fields for the FP32-basis form (a=v0^2 / r)
