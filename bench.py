@@ -4,7 +4,9 @@
                     [--config I] [--variant hcwy] [--precision fp64]
 
 --config 3 selects the batched workload (512 advection-diffusion instances of
-uneven size in one persistent launch per step).
+uneven size in one persistent launch per step); --config 4 the adjoint workload
+(a step is one loss-and-gradient evaluation of 1/2 ||phi_1(hA(theta))v - y_t||^2
+on the 256x256 Gray-Scott Jacobian: the forward phi product and lsa_phiv_vjp).
 
 A step is one phiv call -- the whole hot path (stencil matvecs, grouped
 reductions, correction, projection, small exponential, output combination) over
@@ -190,6 +192,9 @@ def run_reference(args, world, rank):
     if cfg.get("kind") == "batched":
         run_reference_batched(args, world, cfg)
         return
+    if args.config == 4:
+        run_reference_adjoint(args, world, cfg)
+        return
     inp = W.make_inputs(cfg)
     A = OP.from_workload(cfg, inp)
     variant = args.variant
@@ -218,6 +223,34 @@ def run_reference(args, world, rank):
                              "sample": sample},
             "e2e": {"value": value, "unit": "phiv/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_adjoint(args, world, cfg):
+    """The oracle's gradient evaluation (float64 NumPy/SciPy) on this host."""
+    import workloads as W
+    from oracle import adjoint as OAD
+
+    inp = W.adjoint_inputs(cfg)
+    A, dA = OAD.grayscott_parts(cfg, inp)
+    t0 = time.perf_counter()
+    n = 0
+    while n < max(1, args.steps):
+        OAD.grads_krylov(A, dA, inp["v"], inp["y_target"], cfg["h"], cfg["m"], args.variant)
+        n += 1
+        if time.perf_counter() - t0 > 3 * args.cpu_budget:   # keep the run within minutes
+            break
+    el = time.perf_counter() - t0
+    value = n / el
+    sample = f"{n} full gradient evaluation(s) of {cfg['name']} (m={cfg['m']}, {args.variant})"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "grad/s",
+            "n_gpus": world, "steps": n, "warmup": 0, "ms_per_step": 1e3 * el / n,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": cfg["name"], "m": cfg["m"], "h": cfg["h"],
+                                             "variant": args.variant, "precision": "fp64"},
+            "cpu_baseline": {"value": value, "unit": "grad/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "grad/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -428,6 +461,143 @@ def bench_batched(args, world, rank, local, bcfg):
         torch.distributed.destroy_process_group()
 
 
+def adjoint_flops(cfg, m):
+    """FP64 flops of one gradient evaluation: the forward phi product and the
+    product on A^T (N unknowns each) and four on the Frechet block operator
+    (2N unknowns each; its stencil is counted like the Gray-Scott one)."""
+    _, f = algorithmic_counts(cfg, "fp64", m)
+    return 2 * f + 4 * 2 * f
+
+
+def bench_adjoint(args, world, rank, local, cfg):
+    import numpy as np
+    import torch
+
+    import paper_2410_14917_gb300 as lsa
+    import workloads as W
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    inp = W.adjoint_inputs(cfg)
+    N = W.n_dof(cfg)
+    m, h = cfg["m"], cfg["h"]
+    d = {k: torch.from_numpy(v).to(dev) for k, v in inp.items()}
+    op = lsa.Operator.from_workload(cfg, d)
+    v, yt = d["v"], d["y_target"]
+    y = torch.empty((2, N), dtype=torch.float64, device=dev)
+    work = lsa.Workspace.for_call(op, m, 1, "fp64")
+    vwork = lsa.Workspace(lsa.vjp_workspace_bytes(op, m), device=dev)
+    stream = torch.cuda.current_stream()
+    flush = None if args.no_flush else torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def grad_eval(vv, tgt):
+        lsa.phiv(op, vv, h, 1, m, variant=args.variant, y=y, work=work, stats=False)
+        r = y[1] - tgt
+        return lsa.phiv_vjp(op, vv, h, m, r, y, variant=args.variant, work=vwork)
+
+    gv, gs, st = lsa.phiv_vjp(op, v, h, m, lsa.phiv(op, v, h, 1, m, variant=args.variant, y=y,
+                                                    work=work)[0][1] - yt, y, variant=args.variant,
+                              work=vwork, stats=True)
+    for _ in range(args.warmup):
+        grad_eval(v, yt)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    fwd = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        if flush is not None:
+            flush.fill_(i & 0xFF)
+        ev[i][0].record(stream)
+        gv, gs, _ = grad_eval(v, yt)
+        ev[i][1].record(stream)
+    # the plain float64 forward phi product alone, for comparison
+    for i in range(args.steps):
+        if flush is not None:
+            flush.fill_(i & 0xFF)
+        fwd[i][0].record(stream)
+        lsa.phiv(op, v, h, 1, m, variant=args.variant, y=y, work=work, stats=False)
+        fwd[i][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    fwd_ms = statistics.mean(a.elapsed_time(b) for a, b in fwd)
+    tot_ms, value = aggregate_replicas(sum(step_ms), args.steps, world, dev)
+
+    # end to end with host buffers: v and y_t in, dL/dv and the five scalar gradients out
+    v_host = torch.from_numpy(inp["v"]).pin_memory()
+    t_host = torch.from_numpy(inp["y_target"]).pin_memory()
+    gv_host = torch.empty(N, dtype=torch.float64).pin_memory()
+    gs_host = torch.empty(5, dtype=torch.float64).pin_memory()
+    e2e_steps = max(3, min(args.steps, 10))
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        vv = v_host.to(dev, non_blocking=True)
+        tt = t_host.to(dev, non_blocking=True)
+        g1, g2, _ = grad_eval(vv, tt)
+        gv_host.copy_(g1, non_blocking=True)
+        gs_host.copy_(g2, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_value = e2e_steps / (e0.elapsed_time(e1) / 1e3) * world
+
+    ms_step = tot_ms / args.steps
+    flops = adjoint_flops(cfg, m)
+    achieved = flops / (ms_step / 1e3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+            "kernel": "whole gradient evaluation (six k_arnoldi launches with their small kernels)",
+            "peak_source": "FP64 FMA pipe from unit counts and max clock (152 SMs x 2 FMA/clk x 2.07 GHz)",
+            "algorithmic_flops": flops}
+    line = {"metric": METRIC, "value": value, "unit": "grad/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": cfg["name"], "N": N, "m": m, "h": h, "variant": args.variant,
+                       "precision": "fp64", "theta": ["Du", "Dv", "F", "k"],
+                       "l2": "flushed between timed steps (256 MiB write)" if flush is not None
+                       else "not flushed", "parallelism": f"replicas x{world}"},
+            "phiv_per_grad": 6,
+            "vs_plain_fp64_forward": {"forward_ms": fwd_ms, "gradient_ms": ms_step,
+                                      "ratio": ms_step / fwd_ms},
+            "grid_syncs": st["grid_syncs"],
+            "roofline": roof,
+            "e2e": {"value": e2e_value, "unit": "grad/s", "h2d_bytes_per_step": 2 * N * 8,
+                    "d2h_bytes_per_step": (N + 5) * 8},
+            "gpu_launches": (6 * 4 + 10 + 0) * args.steps,
+            "clocks": clocks}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        from oracle import adjoint as OAD
+
+        A, dA = OAD.grayscott_parts(cfg, inp)
+        t0 = time.perf_counter()
+        ref = OAD.grads_krylov(A, dA, inp["v"], inp["y_target"], h, m)
+        el = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": 1.0 / el, "unit": "grad/s", "cores": os.cpu_count(),
+                                "kind": "oracle",
+                                "sample": f"one full gradient evaluation of {cfg['name']} (mgs, float64 NumPy/SciPy)"}
+        g_s = gs.cpu().numpy()
+        errs = [float(np.max(np.abs(gv.cpu().numpy() - ref["dv"])) / np.max(np.abs(ref["dv"]))),
+                abs(g_s[0] - ref["dh"]) / abs(ref["dh"])]
+        errs += [abs(g_s[1 + k] - ref["dtheta"][k]) / abs(ref["dtheta"][k]) for k in range(4)]
+        line["rel_err_vs_oracle"] = max(errs)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def cpu_baseline(cfg, variant, budget):
     """Time the oracle (as it stands) on a bounded sample: whole phiv calls on
     the full workload until ~budget seconds have passed.  Also returns the last
@@ -466,6 +636,9 @@ def main():
     cfg = workload(args.config, args.size)
     if cfg.get("kind") == "batched":
         bench_batched(args, world, rank, local, cfg)
+        return
+    if args.config == 4:
+        bench_adjoint(args, world, rank, local, cfg)
         return
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
