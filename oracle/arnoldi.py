@@ -78,6 +78,40 @@ def cgs2(matvec, b, m):
                 syncs=syncs, fallbacks=0, breakdown=m_eff < m)
 
 
+def iocgs(matvec, b, m, nprev=2):
+    """Incomplete orthogonalisation (Sect. 2.3.1, IOP; the paper's reference
+    baseline ioCGS): A v_j is orthogonalised against the previous ``nprev``
+    basis vectors only, classically -- their inner products in one global
+    sync, then the norm in a second (2 syncs per step).  The basis is not
+    orthonormal and H is banded (entries j-nprev+1..j+1 of column j); the phi
+    products use H and V as they are."""
+    b = np.asarray(b, dtype=np.float64)
+    N = b.size
+    V = np.zeros((N, m + 1))
+    H = np.zeros((m + 1, m))
+    beta = np.linalg.norm(b)
+    V[:, 0] = b / beta
+    syncs = []
+    m_eff = m
+    for j in range(1, m + 1):
+        w = matvec(V[:, j - 1])
+        nrm_aw = np.linalg.norm(w)
+        lo = max(1, j - nprev + 1)              # v_lo .. v_j
+        Vp = V[:, lo - 1:j]
+        h = Vp.T @ w                            # global sync
+        w = w - Vp @ h
+        H[lo - 1:j, j - 1] = h
+        nrm = np.linalg.norm(w)                 # global sync
+        syncs.append(2)
+        H[j, j - 1] = nrm
+        if nrm <= BREAKDOWN_TOL * nrm_aw:
+            m_eff = j
+            break
+        V[:, j] = w / nrm
+    return dict(V=V[:, :m_eff + 1], H=H[:m_eff + 1, :m_eff], beta=beta, m_eff=m_eff,
+                syncs=syncs, fallbacks=0, breakdown=m_eff < m)
+
+
 # ---------------------------------------------------------------------------
 # Correction matrices of the hybrid method.  ``temp`` is the (j+1) x 2 array of
 # Alg. 4 after its scalings; j is the paper's step index (1-based).
@@ -218,7 +252,7 @@ def hybrid(matvec, b, m, variant="hcwy"):
                 fallbacks=fallbacks, breakdown=m_eff < m)
 
 
-VARIANTS = {"mgs": mgs, "cgs2": cgs2,
+VARIANTS = {"mgs": mgs, "cgs2": cgs2, "iocgs": iocgs,
             "hcwy": lambda f, b, m: hybrid(f, b, m, "hcwy"),
             "hncwy": lambda f, b, m: hybrid(f, b, m, "hncwy"),
             "hgsmgs": lambda f, b, m: hybrid(f, b, m, "hgsmgs")}

@@ -377,3 +377,42 @@ def pin_adjoint_finite_differences(n=8, eps=1e-6, m=60):
         fd = (L_at(theta=th + e) - L_at(theta=th - e)) / (2 * eps)
         errs.append(abs(fd - g["dtheta"][k]) / max(abs(g["dtheta"][k]), 1e-12))
     return max(errs)
+
+
+# --- incomplete orthogonalisation (ioCGS) -----------------------------------
+
+def pin_iocgs_symmetric_is_lanczos():
+    """For a symmetric operator the two-vector incomplete process is Lanczos,
+    which spans the same Krylov space with the same (tridiagonal) H as full
+    orthogonalisation: ioCGS must match MGS (small m, little loss of
+    orthogonality)."""
+    cfg = W.advdiff2d(24, ny=20, vel=(0.0, 0.0), diff=0.02, m=12)
+    A = OP.from_workload(cfg, {})
+    b = np.random.default_rng(4).uniform(-1, 1, A.shape[0])
+    r_io = OA.iocgs(lambda x: A @ x, b, cfg["m"])
+    r_mg = OA.mgs(lambda x: A @ x, b, cfg["m"])
+    return max(float(np.abs(r_io["H"] - r_mg["H"]).max() / np.abs(r_mg["H"]).max()),
+               float(np.abs(r_io["V"] - r_mg["V"]).max()))
+
+
+def pin_iocgs_defining_properties():
+    """On a non-symmetric operator: unit basis vectors, each new vector
+    orthogonal to the two it was orthogonalised against, the banded relation
+    A v_j = sum_{i=j-1}^{j+1} H_ij v_i, and H zero outside that band."""
+    cfg = W.advdiff2d(20, ny=18, m=15)
+    A = OP.from_workload(cfg, {})
+    b = np.random.default_rng(8).uniform(-1, 1, A.shape[0])
+    r = OA.iocgs(lambda x: A @ x, b, cfg["m"])
+    V, H, m = r["V"], r["H"], r["m_eff"]
+    err = float(np.abs(np.linalg.norm(V, axis=0) - 1).max())
+    for j in range(1, m + 1):
+        for i in range(max(1, j - 1), j + 1):
+            err = max(err, abs(float(V[:, j] @ V[:, i - 1])))
+        band = slice(max(0, j - 2), j + 1)
+        err = max(err, float(np.linalg.norm(A @ V[:, j - 1] - V[:, band] @ H[band, j - 1]))
+                  / float(np.linalg.norm(A @ V[:, j - 1])))
+        mask = np.ones(m + 1, bool)
+        mask[band] = False
+        err = max(err, float(np.abs(H[mask, j - 1]).max(initial=0.0)))
+    # it is not full orthogonalisation: distant vectors do lose orthogonality
+    return err

@@ -112,3 +112,9 @@ def test_adjoint_derivative_sign_slip_is_caught(monkeypatch):
     # the dense reference shares dA with the Krylov gradients: the central
     # differences of the loss are the pin that sees this slip
     assert pins.pin_adjoint_finite_differences() > 1e-3
+
+
+def test_iocgs_window_slip_is_caught(monkeypatch):
+    orig = OA.iocgs
+    monkeypatch.setattr(OA, "iocgs", lambda f, b, m, nprev=2: orig(f, b, m, nprev=1))
+    assert pins.pin_iocgs_symmetric_is_lanczos() > 1e-3 or pins.pin_iocgs_defining_properties() > 1e-3

@@ -101,3 +101,11 @@ def test_h_zero(variant):
 
 def test_sync_counts():
     assert pins.pin_sync_counts() == 0
+
+
+def test_iocgs_symmetric_operator_is_lanczos():
+    assert pins.pin_iocgs_symmetric_is_lanczos() < 1e-9
+
+
+def test_iocgs_defining_properties():
+    assert pins.pin_iocgs_defining_properties() < 1e-12
