@@ -51,7 +51,8 @@ typedef enum {
   LSA_ERR_WORKSPACE = -5    /* workspace too small or misaligned (needs 256-byte alignment) */
 } lsa_status;
 
-typedef enum { LSA_MGS = 0, LSA_CGS2 = 1, LSA_HCWY = 2, LSA_HNCWY = 3, LSA_HGSMGS = 4 } lsa_variant;
+typedef enum { LSA_MGS = 0, LSA_CGS2 = 1, LSA_HCWY = 2, LSA_HNCWY = 3, LSA_HGSMGS = 4,
+               LSA_IOCGS = 5 } lsa_variant;
 
 /* LSA_FP64: basis, matvec and all reductions in IEEE double.
  * LSA_FP32_BASIS: basis vectors and the stencil matvec in float; inner products
@@ -150,7 +151,9 @@ lsa_status lsa_matvec(const lsa_op* op, const void* x, void* y, int precision,
  *  H  dev, (m+1) x m column-major doubles (leading dimension m+1); entries
  *     outside the leading (m_eff+1) x m_eff block are set to zero.
  * Sync count: LSA_MGS j+1 at step j (plus one for ||v||), LSA_CGS2 3 per step
- * (plus one), hybrid variants 1 per step plus 1 final (plus one per fallback). */
+ * (plus one), LSA_IOCGS 2 per step (plus one), hybrid variants 1 per step plus
+ * 1 final (plus one per fallback).  With LSA_IOCGS the columns are unit vectors
+ * orthogonal to their two predecessors only. */
 lsa_status lsa_arnoldi(const lsa_op* op, const double* v, int m, int variant, int precision,
                        void* V, double* H, void* work, size_t work_bytes,
                        lsa_stats* stats, void* stream);

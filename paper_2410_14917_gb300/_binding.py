@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "liblsarnoldi.so")
 LSA_OK, LSA_BREAKDOWN, LSA_NOT_CONVERGED = 0, 1, 2
 LSA_ERR_ARG, LSA_ERR_CUDA, LSA_ERR_TIMEOUT, LSA_ERR_NUMERIC, LSA_ERR_WORKSPACE = -1, -2, -3, -4, -5
 
-VARIANTS = {"mgs": 0, "cgs2": 1, "hcwy": 2, "hncwy": 3, "hgsmgs": 4}
+VARIANTS = {"mgs": 0, "cgs2": 1, "hcwy": 2, "hncwy": 3, "hgsmgs": 4, "iocgs": 5}
 PRECISIONS = {"fp64": 0, "fp32": 1}
 KINDS = {"advdiff2d": 1, "grayscott2d": 2, "adr3d": 3, "grayscott2d_t": 4, "grayscott2d_frechet": 5}
 

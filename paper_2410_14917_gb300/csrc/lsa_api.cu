@@ -139,7 +139,7 @@ int arnoldi_blocks_per_sm(const DevOp& d, int precision) {
 // alignment rules (LSA_TMA=0 in the environment disables it, LSA_TMA=1 also
 // allows it for the float64 form).
 static bool use_tma(const ArnoldiParams& P, int precision) {
-  if (P.variant < LSA_HCWY || P.op.kind > LSA_OP_ADR3D) return false;
+  if (!is_hybrid(P.variant) || P.op.kind > LSA_OP_ADR3D) return false;
   const char* env = getenv("LSA_TMA");
   if (env && env[0] == '0') return false;
   if (precision == LSA_FP64 && !(env && env[0] == '1')) return false;
@@ -153,7 +153,7 @@ static bool use_tma(const ArnoldiParams& P, int precision) {
 // operators whenever its stages fit (LSA_STREAM=0 in the environment disables
 // it; the other kernels then run).
 static bool use_stream(const ArnoldiParams& P, int precision) {
-  if (P.variant < LSA_HCWY || precision != LSA_FP32_BASIS || !P.E) return false;
+  if (!is_hybrid(P.variant) || precision != LSA_FP32_BASIS || !P.E) return false;
   const char* env = getenv("LSA_STREAM");
   if (env && env[0] == '0') return false;
   if (P.op.kind == LSA_OP_ADVDIFF2D) return stream_applicable_advdiff2d(P.op, P.tl, P.m);
@@ -381,7 +381,7 @@ lsa_status lsa_arnoldi(const lsa_op* op, const double* v, int m, int variant, in
                        void* V, double* H, void* work, size_t work_bytes, lsa_stats* stats,
                        void* stream) {
   if (!v || !V || !H) return LSA_ERR_ARG;
-  if (variant < LSA_MGS || variant > LSA_HGSMGS) return LSA_ERR_ARG;
+  if (variant < LSA_MGS || variant > LSA_IOCGS) return LSA_ERR_ARG;
   long long N = lsa_op_dof(op);
   if (N < 1 || m > N) return LSA_ERR_ARG;
   Prepared pr;
@@ -400,7 +400,7 @@ lsa_status lsa_arnoldi(const lsa_op* op, const double* v, int m, int variant, in
   if (e == cudaSuccess) e = launch_arnoldi(P, precision, pr.L.G, s);
   tm.mark(1);
   if (e == cudaSuccess)
-    e = launch_copy_basis(V, P.V, precision, N, m, P.ctl, variant >= LSA_HCWY ? 1 : 0, s);
+    e = launch_copy_basis(V, P.V, precision, N, m, P.ctl, is_hybrid(variant) ? 1 : 0, s);
   if (e != cudaSuccess) return LSA_ERR_CUDA;
   if (stats) {
     lsa_status r = fill_stats(P.ctl, stats, s);
@@ -416,7 +416,7 @@ lsa_status lsa_phiv(const lsa_op* op, const double* v, double h, int p, int m, d
                     int variant, int precision, double* y, void* work, size_t work_bytes,
                     lsa_stats* stats, void* stream) {
   if (!v || !y) return LSA_ERR_ARG;
-  if (variant < LSA_MGS || variant > LSA_HGSMGS) return LSA_ERR_ARG;
+  if (variant < LSA_MGS || variant > LSA_IOCGS) return LSA_ERR_ARG;
   if (p < 0 || p > PMAX || !isfinite(h) || isnan(tol)) return LSA_ERR_ARG;
   long long N = lsa_op_dof(op);
   if (N < 1 || m < 1) return LSA_ERR_ARG;

@@ -224,7 +224,7 @@ lsa_status lsa_batch_create(const lsa_op* ops, const int* m, int count, double h
                             lsa_batch** out, void* stream) {
   if (!out) return LSA_ERR_ARG;
   *out = nullptr;
-  if (variant < LSA_MGS || variant > LSA_HGSMGS) return LSA_ERR_ARG;
+  if (variant < LSA_MGS || variant > LSA_IOCGS) return LSA_ERR_ARG;
   if (!isfinite(h) || isnan(tol)) return LSA_ERR_ARG;
   lsa_batch* b = new (std::nothrow) lsa_batch();
   if (!b) return LSA_ERR_ARG;

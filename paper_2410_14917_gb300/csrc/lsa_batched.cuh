@@ -123,6 +123,7 @@ __device__ __noinline__ bool batch_instance(const BatchParams& BP, const BatchIn
     e.gsize = gsize;
     if (P.variant == LSA_MGS) e.run_mgs(false);
     else if (P.variant == LSA_CGS2) e.run_cgs2(false);
+    else if (P.variant == LSA_IOCGS) e.run_iocgs(false);
     else e.run_hybrid();
   }
   __syncthreads();

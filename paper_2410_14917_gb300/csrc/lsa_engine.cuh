@@ -818,6 +818,49 @@ struct Engine {
     }
     if (write_vlast) write_last(V + (long long)m * N, Wb[m & 1]);
   }
+
+  // Incomplete orthogonalisation (Sect. 2.3.1, the paper's baseline ioCGS):
+  // A v_j against v_{j-1} and v_j only, classically -- both inner products in
+  // one reduction, then the norm (2 reductions per step).
+  __device__ void run_iocgs(bool write_vlast) {
+    B* V = reinterpret_cast<B*>(P.V);
+    B* Wb[2] = {reinterpret_cast<B*>(P.W0), reinterpret_cast<B*>(P.W1)};
+    const long long N = P.op.N;
+    const int m = P.m;
+    unsigned gen = 0;
+    if (!norm_of_input(gen)) return;
+    if (S.done) return;
+    for (int j = 1; j <= m; ++j) {
+      B* w = Wb[j & 1];
+      const int lo = j >= 2 ? j - 2 : 0;   // columns lo..j-1: v_{j-1} (if any), v_j
+      // v_j = a * (previous w or b); w = A v_j; v_{j-1} . w; v_j . w; ||w||^2
+      PassT<B> pa;
+      pa.c0 = pa.c1 = 0; pa.a = (double)S.a;
+      pa.src64 = (j == 1) ? P.vin : nullptr;
+      pa.srcB = (j == 1) ? nullptr : Wb[(j - 1) & 1];
+      pa.xout = V + (long long)(j - 1) * N; pa.wout = w;
+      pa.d0 = lo; pa.d1 = j - 1; pa.dmode = DOT_W;
+      pa.self = SELF_XW | SELF_WW;
+      int ns = run_pass(pa);
+      if (!reduce_step(gen, ns, j, [&] {
+            const int nd = j - 1 - lo;
+            for (int i = lo + tid; i < j; i += NT) {
+              double h = (i < j - 1) ? S.red[nd + i - lo] : S.red[2 * nd + 1];
+              Hat(i, j - 1) = h;
+              P.ctl->coef[i] = h;
+            }
+            if (tid == 0) { P.ctl->aw_prev = sqrt(S.red[2 * nd + 2]); P.ctl->syncs += 1; }
+          })) return;
+      // w -= H_{lo..j,j} v_{lo..j}; ||w||
+      PassT<B> pc;
+      pc.c0 = lo; pc.c1 = j; pc.a = 1.0; pc.src64 = nullptr; pc.srcB = w;
+      pc.xout = w; pc.wout = nullptr; pc.d0 = pc.d1 = 0; pc.dmode = 0; pc.self = SELF_XX;
+      int nc = run_pass(pc);
+      if (!reduce_step(gen, nc, 0, [&] { finish_norm(j); })) return;
+      if (S.done) return;
+    }
+    if (write_vlast) write_last(V + (long long)m * N, Wb[m & 1]);
+  }
 };
 
 #ifndef LSA_MINB_F64
@@ -836,6 +879,7 @@ __global__ void __launch_bounds__(NT, (sizeof(Tc) == 8) ? LSA_MINB_F64 : LSA_MIN
   E e(P, S, reinterpret_cast<double*>(smem_raw + E::small_offset()));
   if (P.variant == LSA_MGS) e.run_mgs(P.write_vlast != 0);
   else if (P.variant == LSA_CGS2) e.run_cgs2(P.write_vlast != 0);
+  else if (P.variant == LSA_IOCGS) e.run_iocgs(P.write_vlast != 0);
   else e.run_hybrid();
 }
 

@@ -102,6 +102,11 @@ struct Layout {
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// The one-reduce hybrid variants (Alg. 4 with Algs. 5/6/7).
+__host__ __device__ inline bool is_hybrid(int variant) {
+  return variant >= LSA_HCWY && variant <= LSA_HGSMGS;
+}
+
 // Edge array of the streaming float32 kernel.  For every extended-basis
 // column and every TX x TY tile (bx, by) of plane z it holds the tile's
 // periodic x-halo: the TY values left of the tile (x = x0-1), then the TY

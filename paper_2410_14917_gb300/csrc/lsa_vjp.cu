@@ -122,7 +122,7 @@ lsa_status lsa_phiv_vjp(const lsa_op* op, const double* v, double h, int m, int 
                         void* work, size_t work_bytes, lsa_stats* stats, void* stream) {
   if (!v || !r || !y || !grad_v || !grad_s) return LSA_ERR_ARG;
   if (!isfinite(h) || h == 0.0) return LSA_ERR_ARG;
-  if (variant < LSA_MGS || variant > LSA_HGSMGS || m < 1 || m > MMAX) return LSA_ERR_ARG;
+  if (variant < LSA_MGS || variant > LSA_IOCGS || m < 1 || m > MMAX) return LSA_ERR_ARG;
   VjpLayout L;
   long long N = 0;
   if (!vjp_layout(op, m, &L, &N)) return LSA_ERR_ARG;

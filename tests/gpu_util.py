@@ -52,4 +52,6 @@ def expected_syncs(variant, m_eff, fallbacks=0):
         return 1 + sum(j + 1 for j in range(1, m_eff + 1))
     if variant == "cgs2":
         return 1 + 3 * m_eff
+    if variant == "iocgs":
+        return 1 + 2 * m_eff
     return m_eff + 1 + fallbacks
