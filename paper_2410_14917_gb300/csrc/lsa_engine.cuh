@@ -272,16 +272,21 @@ struct Engine {
         }
         const Tc* v = vb[kk & 1];
         if constexpr (F64) {
-          double px0 = 0, pw0 = 0, px1 = 0, pw1 = 0;   // two chains each: more FP64 ILP
+          // straight into the per-column accumulators: every FP64 instruction
+          // is a product term (the FP64 pipe is the bound; the independent
+          // columns of a warp give the ILP)
+          if (dx) {
+            double a = ax[kk];
 #pragma unroll
-          for (int k = 0; k < NPS; k += 2) {
-            px0 = fma((double)v[k], (double)xv[k], px0);
-            pw0 = fma((double)v[k], (double)wv[k], pw0);
-            px1 = fma((double)v[k + 1], (double)xv[k + 1], px1);
-            pw1 = fma((double)v[k + 1], (double)wv[k + 1], pw1);
+            for (int k = 0; k < NPS; ++k) a = fma((double)v[k], (double)xv[k], a);
+            ax[kk] = a;
           }
-          if (dx) ax[kk] += px0 + px1;
-          if (dw) aw[kk] += pw0 + pw1;
+          if (dw) {
+            double a = aw[kk];
+#pragma unroll
+            for (int k = 0; k < NPS; ++k) a = fma((double)v[k], (double)wv[k], a);
+            aw[kk] = a;
+          }
         } else {
           float px = 0.f, pw = 0.f;
 #pragma unroll
