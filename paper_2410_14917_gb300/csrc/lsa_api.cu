@@ -208,6 +208,7 @@ static bool make_layout(const DevOp& d, int m, int precision, Layout* L) {
   auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
   L->ctl = take(sizeof(Ctl));
   L->partials = take((size_t)sms * (bps > 2 ? bps : 2) * SLOTS * sizeof(double));
+  L->gsum = take((size_t)RG_MAX * SLOTS * sizeof(double));
   L->T = take((size_t)MMAX * MMAX * sizeof(double));
   L->L = take((size_t)MMAX * MMAX * sizeof(double));
   L->H = take((size_t)(m + 1) * m * sizeof(double));
@@ -312,6 +313,7 @@ static lsa_status prepare(const lsa_op* op, int m, int precision, void* work, si
   P.tl = make_tiling(pr->d);
   P.ctl = (Ctl*)(pr->w + pr->L.ctl);
   P.partials = (double*)(pr->w + pr->L.partials);
+  P.gsum = (double*)(pr->w + pr->L.gsum);
   P.T = (double*)(pr->w + pr->L.T);
   P.L = (double*)(pr->w + pr->L.L);
   P.V = pr->w + pr->L.V;

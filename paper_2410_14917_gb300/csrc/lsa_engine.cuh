@@ -399,6 +399,28 @@ struct Engine {
     __syncthreads();
   }
 
+  // Two-level form.  Level 1: the last CTA of group g (CTAs g*RG .. g*RG+gn-1)
+  // sums the group's partials into gsum row g; level 2: the last group to
+  // finish sums the group rows into S.red.  One thread per slot, so the loads
+  // of a warp are contiguous; each thread adds its rows in index order, so the
+  // result is deterministic for a given grid.
+  __device__ void sum_rows(const double* src, int nrows, int nslots, double* dst, bool to_smem) {
+    for (int s = tid; s < nslots; s += NT) {
+      double acc = 0.0;
+      int r = 0;
+      for (; r + 8 <= nrows; r += 8) {
+        double v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = __ldcg(src + (long long)(r + i) * SLOTS + s);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) acc += v[i];
+      }
+      for (; r < nrows; ++r) acc += __ldcg(src + (long long)r * SLOTS + s);
+      if (to_smem) dst[s] = acc;
+      else __stcg(dst + s, acc);
+    }
+  }
+
   // Read the published control state into shared memory (all threads).
   __device__ void load_ctl(int ncoef) {
     for (int c = tid; c < ncoef; c += NT) S.coefc[c] = (Tc)__ldcg(&P.ctl->coef[c]);
@@ -414,10 +436,23 @@ struct Engine {
   template <class Fn>
   __device__ bool reduce_step(unsigned& gen, int nslots, int ncoef_after, Fn fn) {
     const BarrierRef br = arnoldi_barrier(P.ctl);
-    int r = barrier_arrive(br, gen, gsize, &S.flag, P.timeout_ns);
+    int r;
+    if (P.gsum == nullptr || gsize > RG * RG_MAX) {
+      r = barrier_arrive(br, gen, gsize, &S.flag, P.timeout_ns);
+      if (r == 1) reduce_partials(nslots);
+    } else {
+      const int grp = grank / RG, g0 = grp * RG;
+      const int gn = min(RG, gsize - g0), ngr = (gsize + RG - 1) / RG;
+      const int lead = counter_arrive(&P.ctl->g_arrive[grp], gen, gn, &S.flag);
+      if (lead) sum_rows(P.partials + (long long)g0 * SLOTS, gn, nslots, P.gsum + (long long)grp * SLOTS, false);
+      r = barrier_arrive(br, gen, ngr, &S.flag, P.timeout_ns, lead != 0);
+      if (r == 1) {
+        sum_rows(P.gsum, ngr, nslots, S.red, true);
+        __syncthreads();
+      }
+    }
     if (r < 0) return false;
     if (r == 1) {
-      reduce_partials(nslots);
       fn();
       __syncthreads();
       if (tid == 0) { P.ctl->barriers += 1; }

@@ -19,6 +19,8 @@ constexpr int PS = PW * PH;               // plane size in shared memory
 constexpr int KMAX = (MMAX + NW - 1) / NW; // basis columns per warp in the dot phase
 constexpr int NMAX_SMALL = MMAX + PMAX + 1; // largest augmented Hessenberg size
 constexpr int SMALL_STRIDE = NMAX_SMALL;    // leading dimension of small dense matrices
+constexpr int RG = 32;                    // CTAs per group of the two-level grid reduction
+constexpr int RG_MAX = 64;                // groups of the two-level grid reduction (G <= RG * RG_MAX)
 
 // Device-side control block, one per workspace.  Written only by the CTA that
 // arrives last at a grid barrier (between barriers), read by all after it.
@@ -45,6 +47,7 @@ struct Ctl {
   double h_last;           // H_{m+1,m}
   double err_est;
   double red[SLOTS];       // reduced sums of the last reduction
+  unsigned int g_arrive[RG_MAX];  // two-level reduction: arrivals per group of RG CTAs
   double coef[MMAX + 2];   // projection coefficients of the next pass
   double sigma[MMAX + 2];  // lazy scales of the stored basis columns
   double hcol[MMAX + 2];
@@ -84,6 +87,7 @@ struct ArnoldiParams {
   double* H;               // (m+1) x m column-major, leading dimension m+1
   Ctl* ctl;
   double* partials;        // gridDim.x x SLOTS
+  double* gsum;            // two-level reduction: per-group sums, RG_MAX x SLOTS (null: one level)
   double* T;               // MMAX x MMAX correction matrix (CWY/NCWY T, GSMGS M^{-1})
   double* L;               // MMAX x MMAX strictly lower part of V^T V (GSMGS)
   int m;
@@ -96,7 +100,7 @@ struct ArnoldiParams {
 
 // Workspace layout (all offsets 256-byte aligned).
 struct Layout {
-  size_t ctl, partials, T, L, H, V, W0, W1, small, coefs, g0, g1, E, total;
+  size_t ctl, partials, gsum, T, L, H, V, W0, W1, small, coefs, g0, g1, E, total;
   int G;                   // CTAs of the persistent Arnoldi kernel
 };
 
@@ -191,13 +195,18 @@ struct BarrierRef {
   int* status;
 };
 
+// With `arrive` false the CTA only waits for the release (it is not one of
+// the `count` participants).
 __device__ __forceinline__ int barrier_arrive(const BarrierRef& b, unsigned gen, unsigned count,
-                                              int* s_flag, long long timeout_ns) {
+                                              int* s_flag, long long timeout_ns, bool arrive = true) {
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
-    unsigned old = atomicAdd(b.arrive, 1u);
-    int last = (old == (gen + 1u) * count - 1u);
+    int last = 0;
+    if (arrive) {
+      unsigned old = atomicAdd(b.arrive, 1u);
+      last = (old == (gen + 1u) * count - 1u);
+    }
     int res = last ? 1 : 0;
     if (!last) {
       unsigned long long t0 = global_ns();
@@ -220,6 +229,19 @@ __device__ __forceinline__ int barrier_arrive(const BarrierRef& b, unsigned gen,
   __syncthreads();
   int r = *s_flag;
   if (r == 1) __threadfence();
+  return r;
+}
+
+// Arrival at a counter that `count` CTAs reach once per generation, without
+// waiting: returns 1 in the CTA that arrived last.  Must be called by all
+// threads of the CTA.
+__device__ __forceinline__ int counter_arrive(unsigned* ctr, unsigned gen, unsigned count, int* s_flag) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) *s_flag = (atomicAdd(ctr, 1u) == (gen + 1u) * count - 1u);
+  __syncthreads();
+  int r = *s_flag;
+  if (r) __threadfence();
   return r;
 }
 
