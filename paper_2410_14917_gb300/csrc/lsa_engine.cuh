@@ -421,6 +421,45 @@ struct Engine {
     }
   }
 
+  // SM-aware ranks.  CTAs that share an SM share its FP64 pipe and shared
+  // memory bandwidth, so an SM's time is set by the tiles of all its CTAs.
+  // Each CTA records its SM id; after one barrier it takes as rank its place
+  // in the order (slot on its SM, SM id), so the CTAs of one SM are about
+  // G / #SMs ranks apart and, with tiles dealt cyclically by rank, every SM's
+  // tile count is within one of the mean.  The ranks are a permutation of
+  // 0..G-1 and tiles and partials follow the rank, so the results do not
+  // depend on where the CTAs were placed.  Returns false on a timeout.
+  __device__ bool place() {
+    if (tid == 0) {
+      unsigned sm;
+      asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+      unsigned slot = 0;
+      if (sm < (unsigned)SMID_CAP) slot = atomicAdd(&P.ctl->sm_ctas[sm], 1u);
+      else atomicExch(&P.ctl->place_off, 1);
+      S.tmp[0][0] = (double)sm;
+      S.tmp[0][1] = (double)slot;
+    }
+    const BarrierRef br{&P.ctl->p_arrive, &P.ctl->p_release, &P.ctl->abort_flag, &P.ctl->status};
+    const int r = barrier_arrive(br, 0u, gsize, &S.flag, P.timeout_ns);
+    if (r < 0) return false;
+    if (r == 1) barrier_release(br, 0u);
+    __syncthreads();
+    if (warp == 0) {
+      const unsigned sm = (unsigned)S.tmp[0][0], slot = (unsigned)S.tmp[0][1];
+      int rank = 0;
+      for (int s = lane; s < SMID_CAP; s += 32) {
+        const unsigned c = __ldcg(&P.ctl->sm_ctas[s]);
+        rank += (int)min(c, slot) + (((unsigned)s < sm && c > slot) ? 1 : 0);
+      }
+      rank = warp_sum(rank);
+      if (lane == 0) S.flag = __ldcg(&P.ctl->place_off) ? (int)blockIdx.x : rank;
+    }
+    __syncthreads();
+    grank = S.flag;
+    __syncthreads();
+    return true;
+  }
+
   // Read the published control state into shared memory (all threads).
   __device__ void load_ctl(int ncoef) {
     for (int c = tid; c < ncoef; c += NT) S.coefc[c] = (Tc)__ldcg(&P.ctl->coef[c]);
@@ -917,6 +956,7 @@ __global__ void __launch_bounds__(NT, (sizeof(Tc) == 8) ? LSA_MINB_F64 : LSA_MIN
   using E = Engine<Op, Tc, B>;
   typename E::Smem& S = *reinterpret_cast<typename E::Smem*>(smem_raw);
   E e(P, S, reinterpret_cast<double*>(smem_raw + E::small_offset()));
+  if (!e.place()) return;
   if (P.variant == LSA_MGS) e.run_mgs(P.write_vlast != 0);
   else if (P.variant == LSA_CGS2) e.run_cgs2(P.write_vlast != 0);
   else if (P.variant == LSA_IOCGS) e.run_iocgs(P.write_vlast != 0);

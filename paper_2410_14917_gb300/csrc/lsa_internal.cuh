@@ -21,6 +21,7 @@ constexpr int NMAX_SMALL = MMAX + PMAX + 1; // largest augmented Hessenberg size
 constexpr int SMALL_STRIDE = NMAX_SMALL;    // leading dimension of small dense matrices
 constexpr int RG = 32;                    // CTAs per group of the two-level grid reduction
 constexpr int RG_MAX = 64;                // groups of the two-level grid reduction (G <= RG * RG_MAX)
+constexpr int SMID_CAP = 256;             // SM ids tracked by the SM-aware placement
 
 // Device-side control block, one per workspace.  Written only by the CTA that
 // arrives last at a grid barrier (between barriers), read by all after it.
@@ -48,6 +49,10 @@ struct Ctl {
   double err_est;
   double red[SLOTS];       // reduced sums of the last reduction
   unsigned int g_arrive[RG_MAX];  // two-level reduction: arrivals per group of RG CTAs
+  unsigned int p_arrive;   // placement barrier of the persistent Arnoldi kernel
+  unsigned int p_release;
+  int place_off;           // an SM id was out of range: CTA ranks are block indices
+  unsigned int sm_ctas[SMID_CAP];  // CTAs resident per SM id
   double coef[MMAX + 2];   // projection coefficients of the next pass
   double sigma[MMAX + 2];  // lazy scales of the stored basis columns
   double hcol[MMAX + 2];
