@@ -17,6 +17,8 @@ Modules (each function cites the passage of the paper it follows):
              low-synchronisation Arnoldi (Alg. 4 with Algs. 5, 6, 7)
   krylov     O-Krylov: phi_k(hA)v by Krylov projection (Sect. 2.2, Eq. 13,
              with the phi augmentation of Sect. 2.1)
+  lincomb    sum_j tau^j phi_j(tau A) b_j by Krylov projection of the
+             augmented operator (Sect. 2.1, Eqs. 7-9) in equal sub-steps
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test
 against a closed form, a library routine, brute force or a worked example of

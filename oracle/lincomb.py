@@ -1,0 +1,78 @@
+"""Linear combinations of phi-functions by Krylov projection of the augmented
+operator, with fixed sub-stepping (oracle; test infrastructure only, see the
+package docstring).
+
+Sect. 2.1, Eqs. 7-9: for vectors b_0..b_p,
+
+    u(tau) = sum_{j=0}^p tau^j phi_j(tau A) b_j = [I_N 0] exp(tau Aaug) [b_0; e_p],
+    Aaug = [[A, B], [0, K]],  B = [b_p, ..., b_1],  K = [[0, I_{p-1}], [0, 0]].
+
+(The printed Eq. 8 puts tau inside Aaug as well as in front of it; the reading
+used here applies tau once, which is the form that reduces to the left-hand
+side.  It is pinned below against the ODE u' = A u + sum_j t^{j-1}/(j-1)! b_j,
+u(0) = b_0, whose solution the left-hand side is.)
+
+The Krylov process runs on (N+p)-vectors: the product with Aaug is
+A x_top + B x_bot on the first N entries and K x_bot on the last p, so only
+products with A are needed (Sect. 2.1).  u is then the first N entries of
+beta V_m exp(tau H_m) e_1 (Sect. 2.2, Eq. 13, with no phi augmentation of
+H_m).
+
+Sub-stepping (Sect. 2.2, the sub-step product of exponentials): tau is split
+into nsub equal steps dt and w_{s+1} = exp(dt Aaug) w_s, w_0 = [b_0; e_p].
+The last p entries of w evolve under K alone, so at t = s dt they are exactly
+exp(t K) e_p, whose entry p-1-i is t^i / i!; each sub-step restarts from the
+Krylov result for the first N entries and these exact last p entries.  (The
+paper chooses sub-step sizes and dimensions adaptively as in KIOPS, whose
+formulas it does not reproduce; this oracle uses equal steps and a fixed m.)
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from .krylov import phiv
+
+
+def aug_tail(p: int, t: float) -> np.ndarray:
+    """exp(t K) e_p: entry p-1-i is t^i / i! (K the p x p upper shift)."""
+    xi = np.zeros(p)
+    for i in range(p):
+        xi[p - 1 - i] = t ** i / math.factorial(i)
+    return xi
+
+
+def aug_matvec(matvec, bs):
+    """x -> Aaug x for x of length N+p (Eqs. 8-9): [A x_top + B x_bot; K x_bot]."""
+    p = len(bs) - 1
+    N = np.asarray(bs[0]).size
+    cols = [np.asarray(bs[p - k], dtype=np.float64) for k in range(p)]   # B = [b_p, ..., b_1]
+
+    def mv(x):
+        top = np.asarray(matvec(x[:N]), dtype=np.float64).copy()
+        for k in range(p):
+            top += x[N + k] * cols[k]
+        bot = np.zeros(p)
+        bot[:p - 1] = x[N + 1:N + p]
+        return np.concatenate([top, bot])
+
+    return mv
+
+
+def lincomb_krylov(matvec, bs, tau: float, m: int, nsub: int = 1, variant: str = "mgs"):
+    """u = sum_j tau^j phi_j(tau A) b_j in nsub equal sub-steps, each an m-step
+    Krylov projection of Aaug.  Returns (u, infos) with one info per sub-step."""
+    bs = [np.asarray(b, dtype=np.float64) for b in bs]
+    p = len(bs) - 1
+    N = bs[0].size
+    mv = aug_matvec(matvec, bs)
+    dt = tau / nsub
+    u = bs[0].copy()
+    infos = []
+    for s in range(nsub):
+        w0 = np.concatenate([u, aug_tail(p, s * dt)])
+        y, info = phiv(mv, w0, dt, 0, m, variant)
+        u = y[0][:N].copy()
+        infos.append(info)
+    return u, infos

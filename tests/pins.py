@@ -20,6 +20,7 @@ from oracle import arnoldi as OA
 from oracle import exact as OE
 from oracle import expm as OX
 from oracle import krylov as OK
+from oracle import lincomb as OL
 from oracle import operators as OP
 from oracle import phi as OPHI
 
@@ -416,3 +417,70 @@ def pin_iocgs_defining_properties():
         err = max(err, float(np.abs(H[mask, j - 1]).max(initial=0.0)))
     # it is not full orthogonalisation: distant vectors do lose orthogonality
     return err
+
+
+# ---------------------------------------------------------------------------
+# Linear combinations sum_j tau^j phi_j(tau A) b_j (Sect. 2.1, Eqs. 7-9) with
+# sub-stepping (Sect. 2.2).
+
+def _lincomb_case(p, seed, n=6):
+    cfg = W.advdiff2d(n, ny=n, diff=0.05, vel=(1.0, 0.5), m=20)
+    A = OP.from_workload(cfg, {}).toarray()
+    rng = np.random.default_rng(seed)
+    bs = [rng.uniform(-1, 1, A.shape[0]) for _ in range(p + 1)]
+    return A, bs
+
+
+def pin_lincomb_diagonal(p=3, tau=0.7):
+    """A = diag(lam): the combination is sum_j tau^j phi_j(tau lam_i) b_j,i
+    entry by entry (scalar phi_k pinned separately); Krylov with m = N + p
+    spans the whole augmented space, in one and in three sub-steps."""
+    lam = np.array([-3.0, -1.2, -0.4, 0.0, 0.3, 1.1])
+    rng = np.random.default_rng(21)
+    bs = [rng.uniform(-1, 1, lam.size) for _ in range(p + 1)]
+    ref = sum(tau ** j * OPHI.phi(j, tau * lam) * bs[j] for j in range(p + 1))
+    err = 0.0
+    for nsub in (1, 3):
+        u, _ = OL.lincomb_krylov(lambda x: lam * x, bs, tau, lam.size + p, nsub)
+        err = max(err, float(np.abs(u - ref).max() / np.abs(ref).max()))
+    return err
+
+
+def pin_lincomb_solves_forced_ode(p=3, tau=0.4, eps=1e-3):
+    """u(t) = sum_j t^j phi_j(tA) b_j solves u' = A u + sum_{j>=1} t^{j-1}/(j-1)! b_j
+    with u(0) = b_0: a fourth-order central difference in t of the Krylov
+    result against the right-hand side (this fixes where tau enters Eq. 8)."""
+    A, bs = _lincomb_case(p, 22)
+    m = A.shape[0] + p
+    u = lambda t: OL.lincomb_krylov(lambda x: A @ x, bs, t, m, 1)[0]
+    du = (8 * (u(tau + eps) - u(tau - eps)) - (u(tau + 2 * eps) - u(tau - 2 * eps))) / (12 * eps)
+    g = sum(tau ** (j - 1) / math.factorial(j - 1) * bs[j] for j in range(1, p + 1))
+    rhs = A @ u(tau) + g
+    e0 = float(np.abs(u(0.0) - bs[0]).max())
+    return max(float(np.abs(du - rhs).max() / np.abs(rhs).max()), e0)
+
+
+def pin_lincomb_substeps_vs_dense(p=2, tau=1.3):
+    """Dense exponential of the augmented matrix (Eq. 7) against Krylov in 1,
+    2 and 5 equal sub-steps on a non-symmetric operator."""
+    A, bs = _lincomb_case(p, 23)
+    ref = OE.phi_combination_dense(A, bs, tau, expm=scipy.linalg.expm)
+    err = 0.0
+    for nsub in (1, 2, 5):
+        u, _ = OL.lincomb_krylov(lambda x: A @ x, bs, tau, A.shape[0] + p, nsub)
+        err = max(err, float(np.abs(u - ref).max() / np.abs(ref).max()))
+    return err
+
+
+def pin_lincomb_single_vector(p=3, tau=0.9):
+    """Only b_k nonzero: the combination is tau^k phi_k(tau A) b_k, the k-th
+    phi product of the plain path; p = 0 is exp(tau A) b_0 (scipy)."""
+    A, bs = _lincomb_case(p, 24)
+    N = A.shape[0]
+    y, _ = OK.phiv(lambda x: A @ x, bs[p], tau, p, N)
+    zs = [np.zeros(N)] * p + [bs[p]]
+    u, _ = OL.lincomb_krylov(lambda x: A @ x, zs, tau, N + p, 2)
+    err = float(np.abs(u - tau ** p * y[p]).max() / np.abs(tau ** p * y[p]).max())
+    u0, _ = OL.lincomb_krylov(lambda x: A @ x, [bs[0]], tau, N, 1)
+    ref0 = scipy.linalg.expm(tau * A) @ bs[0]
+    return max(err, float(np.abs(u0 - ref0).max() / np.abs(ref0).max()))

@@ -1,0 +1,21 @@
+"""Pins of the oracle's phi-function linear combinations (Sect. 2.1, Eqs. 7-9)
+and their equal sub-steps: closed forms for a diagonal operator, the forced
+ODE the combination solves, dense exponentials of the augmented matrix, and
+the single-vector case of the plain phi products."""
+from tests import pins
+
+
+def test_lincomb_diagonal_closed_form():
+    assert pins.pin_lincomb_diagonal() < 1e-12
+
+
+def test_lincomb_solves_forced_ode():
+    assert pins.pin_lincomb_solves_forced_ode() < 1e-9
+
+
+def test_lincomb_substeps_match_dense_augmented_exponential():
+    assert pins.pin_lincomb_substeps_vs_dense() < 1e-11
+
+
+def test_lincomb_single_vector_is_a_phi_product():
+    assert pins.pin_lincomb_single_vector() < 1e-11

@@ -118,3 +118,24 @@ def test_iocgs_window_slip_is_caught(monkeypatch):
     orig = OA.iocgs
     monkeypatch.setattr(OA, "iocgs", lambda f, b, m, nprev=2: orig(f, b, m, nprev=1))
     assert pins.pin_iocgs_symmetric_is_lanczos() > 1e-3 or pins.pin_iocgs_defining_properties() > 1e-3
+
+
+def test_lincomb_tau_inside_augmented_matrix_is_caught(monkeypatch):
+    # the printed Eq. 8 also scales A by tau inside the augmented matrix
+    from oracle import lincomb as OL
+    orig = OL.aug_matvec
+
+    def bad(matvec, bs):
+        return orig(lambda x: 0.7 * matvec(x), bs)
+    monkeypatch.setattr(OL, "aug_matvec", bad)
+    assert pins.pin_lincomb_solves_forced_ode() > 1e-3
+    assert pins.pin_lincomb_substeps_vs_dense() > 1e-3
+
+
+def test_lincomb_reversed_forcing_columns_are_caught(monkeypatch):
+    # B = [b_1, ..., b_p] instead of [b_p, ..., b_1]
+    from oracle import lincomb as OL
+    orig = OL.aug_matvec
+    monkeypatch.setattr(OL, "aug_matvec", lambda mv, bs: orig(mv, [bs[0]] + list(bs[1:])[::-1]))
+    assert pins.pin_lincomb_solves_forced_ode() > 1e-3
+    assert pins.pin_lincomb_diagonal() > 1e-3
