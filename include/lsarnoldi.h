@@ -169,6 +169,38 @@ lsa_status lsa_phiv(const lsa_op* op, const double* v, double h, int p, int m, d
                     int variant, int precision, double* y, void* work, size_t work_bytes,
                     lsa_stats* stats, void* stream);
 
+/* Linear combination u = sum_{j=0}^p tau^j phi_j(tau A) b_j of phi-function
+ * products (Sect. 2.1, Eqs. 7-9), the quantity an exponential integrator
+ * needs per stage.  It is the first N entries of exp(tau Aaug) [b_0; e_p]
+ * with the (N+p)-sized augmented operator Aaug = [[A, B], [0, K]],
+ * B = [b_p, ..., b_1], K the p x p upper shift.  The Krylov process runs on
+ * (N+p)-vectors: the extra p entries of every basis vector are kept beside
+ * the basis and the stencil adds B x_bot, so only products with A are formed
+ * on the grid (Sect. 2.1).  tau is split into nsub equal sub-steps (Sect. 2.2
+ * sub-stepping: [u; xi] <- exp(dt Aaug) [u; xi], where the extra entries
+ * follow exp(t K) e_p exactly and restart each sub-step); each sub-step is
+ * one Arnoldi projection of dimension m (the paper's KIOPS layer picks sizes
+ * and dimensions adaptively by formulas it does not give; here they are the
+ * caller's).
+ *  b          dev, (p+1) x N doubles: b + j*N = b_j.  Not modified.
+ *  p          0 <= p <= 8 (p = 0: u = exp(tau A) b_0).
+ *  tau        finite; tau = 0 returns u = b_0.
+ *  nsub       sub-steps, 1 <= nsub <= 2^20.
+ *  m          1 <= m <= lsa_max_m() per sub-step (capped at N + p).
+ *  tol        per sub-step a-posteriori check as lsa_phiv (tol <= 0: off).
+ *  op         LSA_OP_ADVDIFF2D, LSA_OP_GRAYSCOTT2D or LSA_OP_ADR3D.
+ *  precision  LSA_FP64 only (the float32-basis form returns LSA_ERR_ARG).
+ *  u          dev, N doubles; may be b_0 itself but must not overlap b_1..b_p.
+ *  work       dev workspace of lsa_workspace_bytes(op, m, 0, LSA_FP64).
+ *  stats      summed over the sub-steps (grid syncs, fallbacks, times),
+ *             smallest m_eff, largest err_est, beta of the first sub-step;
+ *             with stats the call synchronises the stream after each sub-step.
+ * Returns the worst informational status of the sub-steps, or the first
+ * error. */
+lsa_status lsa_phiv_lincomb(const lsa_op* op, const double* b, int p, double tau, int nsub, int m,
+                            double tol, int variant, int precision, double* u, void* work,
+                            size_t work_bytes, lsa_stats* stats, void* stream);
+
 /* S5 alone: coefficients C (dev, (p+2) x m doubles, row k = phi_k(h H_m) e_1,
  * k = 0..p+1) from one exponential of the augmented (m+p+1)-sized matrix,
  * computed on the GPU.  H: dev, column-major with leading dimension ldh >= m. */

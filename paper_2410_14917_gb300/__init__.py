@@ -19,7 +19,7 @@ import torch
 from . import _binding as B
 from ._binding import LsaError, LsaOp, LsaStats, PRECISIONS, VARIANTS, KINDS
 
-__all__ = ["Operator", "phiv", "phiv_noalloc", "arnoldi", "matvec", "expm_phi", "workspace_bytes", "read_stats",
+__all__ = ["Operator", "phiv", "phiv_lincomb", "phiv_noalloc", "arnoldi", "matvec", "expm_phi", "workspace_bytes", "read_stats",
            "selftest_barrier_timeout", "max_m", "LsaError", "Workspace", "Batch", "phiv_batched",
            "phiv_vjp", "Phi1GrayScott"]
 
@@ -171,6 +171,26 @@ def phiv(op: Operator, v: torch.Tensor, h: float, p: int, m: int, tol: float = 0
                           ctypes.byref(s) if stats else None, _stream_ptr(stream))
     _check(st, "lsa_phiv")
     return y, (s.as_dict() if stats else None)
+
+
+def phiv_lincomb(op: Operator, b: torch.Tensor, tau: float, m: int, nsub: int = 1, tol: float = 0.0,
+                 variant="hcwy", u=None, work=None, stream=None, stats=True):
+    """u = sum_j tau^j phi_j(tau A) b[j] (b: (p+1, N) float64 CUDA tensor) by Krylov
+    projection of the augmented operator in nsub equal sub-steps, each of
+    dimension m; returns (u, stats dict or None)."""
+    if b.dtype != torch.float64 or not b.is_cuda or not b.is_contiguous() or b.dim() != 2:
+        raise ValueError("b must be a contiguous (p+1, N) float64 CUDA tensor")
+    p = b.shape[0] - 1
+    N = b.shape[1]
+    u = torch.empty(N, dtype=torch.float64, device=b.device) if u is None else u
+    work = work or Workspace.for_call(op, min(m, N + p), 0, "fp64")
+    s = LsaStats()
+    st = B.lib().lsa_phiv_lincomb(ctypes.byref(op.c), _ptr(b), int(p), float(tau), int(nsub), int(m),
+                                  float(tol), VARIANTS[variant], PRECISIONS["fp64"], _ptr(u),
+                                  ctypes.c_void_p(work.ptr), work.nbytes,
+                                  ctypes.byref(s) if stats else None, _stream_ptr(stream))
+    _check(st, "lsa_phiv_lincomb")
+    return u, (s.as_dict() if stats else None)
 
 
 def phiv_noalloc(op: Operator, v: torch.Tensor, h: float, p: int, m: int, tol: float = 0.0,

@@ -51,6 +51,9 @@ SIGNATURES = {
                             c_void_p, c_size_t, POINTER(LsaStats), c_void_p]),
     "lsa_phiv": (c_int, [POINTER(LsaOp), c_void_p, c_double, c_int, c_int, c_double, c_int, c_int,
                          c_void_p, c_void_p, c_size_t, POINTER(LsaStats), c_void_p]),
+    "lsa_phiv_lincomb": (c_int, [POINTER(LsaOp), c_void_p, c_int, c_double, c_int, c_int, c_double,
+                                 c_int, c_int, c_void_p, c_void_p, c_size_t, POINTER(LsaStats),
+                                 c_void_p]),
     "lsa_expm_phi": (c_int, [c_void_p, c_int, c_int, c_double, c_int, c_void_p, c_void_p, c_size_t,
                              c_void_p]),
     "lsa_read_stats": (c_int, [c_void_p, POINTER(LsaStats), c_void_p]),

@@ -139,7 +139,7 @@ int arnoldi_blocks_per_sm(const DevOp& d, int precision) {
 // alignment rules (LSA_TMA=0 in the environment disables it, LSA_TMA=1 also
 // allows it for the float64 form).
 static bool use_tma(const ArnoldiParams& P, int precision) {
-  if (!is_hybrid(P.variant) || P.op.kind > LSA_OP_ADR3D) return false;
+  if (!is_hybrid(P.variant) || P.op.kind > LSA_OP_ADR3D || P.naug > 0) return false;
   const char* env = getenv("LSA_TMA");
   if (env && env[0] == '0') return false;
   if (precision == LSA_FP64 && !(env && env[0] == '1')) return false;
@@ -153,7 +153,7 @@ static bool use_tma(const ArnoldiParams& P, int precision) {
 // operators whenever its stages fit (LSA_STREAM=0 in the environment disables
 // it; the other kernels then run).
 static bool use_stream(const ArnoldiParams& P, int precision) {
-  if (!is_hybrid(P.variant) || precision != LSA_FP32_BASIS || !P.E) return false;
+  if (!is_hybrid(P.variant) || precision != LSA_FP32_BASIS || !P.E || P.naug > 0) return false;
   const char* env = getenv("LSA_STREAM");
   if (env && env[0] == '0') return false;
   if (P.op.kind == LSA_OP_ADVDIFF2D) return stream_applicable_advdiff2d(P.op, P.tl, P.m);
@@ -231,6 +231,7 @@ static bool make_layout(const DevOp& d, int m, int precision, Layout* L) {
                      (d.kind == LSA_OP_ADVDIFF2D || (d.kind == LSA_OP_ADR3D && d.nz % t.ZS == 0));
   L->E = take(edges ? (size_t)(m + 3) * (size_t)(d.N / 8) * sizeof(float) : 0);
   if (!edges) L->E = 0;
+  L->xaug = take((size_t)(m + 3) * PMAX * sizeof(double));
   L->total = off;
   L->G = G;
   return true;
@@ -321,6 +322,7 @@ static lsa_status prepare(const lsa_op* op, int m, int precision, void* work, si
   P.W1 = pr->w + pr->L.W1;
   P.H = (double*)(pr->w + pr->L.H);
   P.E = pr->L.E ? (float*)(pr->w + pr->L.E) : nullptr;
+  P.xaug = (double*)(pr->w + pr->L.xaug);
   P.m = m;
   P.brk_tol = precision == LSA_FP64 ? kBreakdownTolFp64 : kBreakdownTolFp32;
   P.timeout_ns = kTimeoutNs;
@@ -470,6 +472,87 @@ lsa_status lsa_phiv(const lsa_op* op, const double* v, double h, int p, int m, d
     return r;
   }
   return LSA_OK;
+}
+
+lsa_status lsa_phiv_lincomb(const lsa_op* op, const double* b, int p, double tau, int nsub, int m,
+                            double tol, int variant, int precision, double* u, void* work,
+                            size_t work_bytes, lsa_stats* stats, void* stream) {
+  if (!b || !u) return LSA_ERR_ARG;
+  if (variant < LSA_MGS || variant > LSA_IOCGS || precision != LSA_FP64) return LSA_ERR_ARG;
+  if (p < 0 || p > PMAX || !isfinite(tau) || nsub < 1 || nsub > (1 << 20) || isnan(tol))
+    return LSA_ERR_ARG;
+  if (!op || op->kind > LSA_OP_ADR3D) return LSA_ERR_ARG;
+  long long N = lsa_op_dof(op);
+  if (N < 1 || m < 1) return LSA_ERR_ARG;
+  if (m > N + p) m = (int)(N + p);
+  Prepared pr;
+  lsa_status st = prepare(op, m, precision, work, work_bytes, &pr);
+  if (st != LSA_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const double dt = tau / nsub;
+  lsa_stats acc;
+  memset(&acc, 0, sizeof(acc));
+  acc.m_eff = m;
+  lsa_status worst = LSA_OK;
+  for (int k = 0; k < nsub; ++k) {
+    // sub-step k: [u; xi] <- exp(dt Aaug) [u; xi], xi = exp(k dt K) e_p exactly
+    ArnoldiParams P = pr.P;
+    P.vin = (k == 0) ? b : u;
+    P.variant = variant;
+    P.write_vlast = 0;
+    P.naug = p;
+    P.baug = b;
+    P.aug_t = k * dt;
+    CallTimer tm(stats != nullptr, s);
+    cudaError_t e = launch_init(P.ctl, pr.d, nullptr, nullptr, precision, P.H, (m + 1) * m, P.vin, P.V, s);
+    tm.mark(0);
+    if (e == cudaSuccess) e = launch_arnoldi(P, precision, pr.L.G, s);
+    tm.mark(1);
+    SmallParams S;
+    memset(&S, 0, sizeof(S));
+    S.H = P.H;
+    S.ldh = m + 1;
+    S.ctl_in = P.ctl;
+    S.ctl = P.ctl;
+    S.m = m;
+    S.p = 0;
+    S.h = dt;
+    S.mats = (double*)(pr.w + pr.L.small);
+    S.C = (double*)(pr.w + pr.L.coefs);
+    S.ldc = MMAX + 2;
+    S.scale_out = 1;
+    S.timeout_ns = kTimeoutNs;
+    S.tol = tol;
+    if (e == cudaSuccess) e = launch_expm(S, s);
+    tm.mark(2);
+    if (e == cudaSuccess) e = launch_combine(P.V, precision, N, S.C, S.ldc, 0, P.ctl, u, s);
+    tm.mark(3);
+    if (e != cudaSuccess) return LSA_ERR_CUDA;
+    if (stats) {
+      lsa_stats one;
+      lsa_status r = fill_stats(P.ctl, &one, s);
+      if (one.m_eff < acc.m_eff) acc.m_eff = one.m_eff;
+      acc.breakdown |= one.breakdown;
+      acc.norm_fallbacks += one.norm_fallbacks;
+      acc.grid_syncs += one.grid_syncs;
+      acc.grid_barriers += one.grid_barriers;
+      if (k == 0) acc.beta = one.beta;
+      if (one.err_est > acc.err_est) acc.err_est = one.err_est;
+      acc.h_last = one.h_last;
+      acc.ms_arnoldi += tm.ms(0, 1);
+      acc.ms_expm += tm.ms(1, 2);
+      acc.ms_combine += tm.ms(2, 3);
+      acc.launches += 4;
+      acc.arnoldi_kernel = arnoldi_kernel_kind(P, precision);
+      if (r < 0) { acc.status = r; *stats = acc; return r; }
+      if (r > worst) worst = r;
+    }
+  }
+  if (stats) {
+    acc.status = worst;
+    *stats = acc;
+  }
+  return worst;
 }
 
 lsa_status lsa_expm_phi(const double* H, int ldh, int m, double h, int p, double* C, void* work,

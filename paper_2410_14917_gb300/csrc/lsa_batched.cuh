@@ -96,6 +96,7 @@ __device__ __noinline__ bool batch_instance(const BatchParams& BP, const BatchIn
     P.ctl = I.ctl;
     P.partials = BP.ws.partials + (size_t)wbase * SLOTS;
     P.gsum = nullptr;
+    P.naug = 0;
     P.T = BP.ws.T + (size_t)wbase * MMAX * MMAX;
     P.L = BP.ws.L + (size_t)wbase * MMAX * MMAX;
     P.m = I.m;

@@ -35,7 +35,10 @@ struct PassT {
 
 __device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
-template <class Op, class Tc, class B>
+// AUG: the augmented operator of Eqs. 8-9 (phi-function linear combinations;
+// float64 only).  A separate instantiation, so that the plain kernels carry
+// none of its code.
+template <class Op, class Tc, class B, bool AUG = false>
 struct Engine {
   static constexpr int NS = Op::NS;
   static constexpr int DIM = Op::DIM;
@@ -51,6 +54,8 @@ struct Engine {
     double tmp[4][MMAX + 2];
     double bred[NW][3];
     double sj, scale, true_nrm, ss;
+    double xi[PMAX], xw[PMAX];       // augmented operator: extra entries of the pass's x and w
+    int aug_xcol, aug_wcol;          // ... and the columns they belong to (-1: not stored)
     Tc a;
     int flag, done, fallback_pending, stop;
   };
@@ -212,6 +217,16 @@ struct Engine {
     long long gpt = (x0 + lx) + (long long)d.nx * ((y0 + ly) + (long long)d.ny * z);
     Tc out[NS];
     Op::template apply<Tc>(d, cf, zm, z0, zp, o, gpt, out);
+    if constexpr (AUG) {         // + B x_bot (augmented operator)
+      const int p = P.naug;
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        double f = (double)out[s];
+        for (int k = 0; k < p; ++k)
+          f = fma(S.xi[k], __ldg(P.baug + (long long)(p - k) * d.N + s * d.npts + gpt), f);
+        out[s] = (Tc)f;
+      }
+    }
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
       Tc wv = out[s];
@@ -301,12 +316,65 @@ struct Engine {
     }
   }
 
+  // -------------------------------------------------------------------------
+  // Augmented operator (Eqs. 8-9).  The extra entries of a vector follow the
+  // same pass formula as its grid points: x_bot = a*src_bot - sum_c coef_c
+  // V_bot,c, and w_bot = K x_bot.  Every CTA forms them at the start of a pass
+  // (p <= PMAX entries, O(p j) work) and the stencil adds B x_bot; CTA rank 0
+  // adds their share to the inner products; the CTA that completes the pass's
+  // reduction stores them (when all CTAs have read the source entries, so an
+  // in-place pass is safe).
+  __device__ __forceinline__ int col_of(const B* ptr) const {
+    return (int)((ptr - reinterpret_cast<const B*>(P.V)) / P.op.N);
+  }
+  __device__ void aug_begin(const PassT<B>& ps) {
+    const int p = P.naug;
+    if (tid < p) {
+      double x;
+      if (ps.src64) {            // the start vector: exp(aug_t K) e_p, entry p-1-i = t^i / i!
+        const int i = p - 1 - tid;
+        double v = 1.0;
+        for (int r = 1; r <= i; ++r) v *= P.aug_t / (double)r;
+        x = ps.a * v;
+      } else {
+        x = ps.a * __ldcg(P.xaug + (long long)col_of(ps.srcB) * PMAX + tid);
+      }
+      for (int c = ps.c0; c < ps.c1; ++c)
+        x = fma(-(double)S.coefc[c], __ldcg(P.xaug + (long long)c * PMAX + tid), x);
+      S.xi[tid] = x;
+    }
+    if (tid == 0) {
+      S.aug_xcol = ps.xout ? col_of(ps.xout) : -1;
+      S.aug_wcol = ps.wout ? col_of(ps.wout) : -1;
+    }
+    __syncthreads();
+    if (tid < p) S.xw[tid] = (tid + 1 < p) ? S.xi[tid + 1] : 0.0;
+    __syncthreads();
+  }
+  // extra-entry share of (column c) . (x or w)
+  __device__ double aug_dot(int c, const double* vec) const {
+    double acc = 0.0;
+    for (int k = 0; k < P.naug; ++k) {
+      const double vc = (c == S.aug_xcol) ? S.xi[k] : __ldcg(P.xaug + (long long)c * PMAX + k);
+      acc = fma(vc, vec[k], acc);
+    }
+    return acc;
+  }
+  __device__ double aug_self(int which) const {
+    const double* a = which == 2 ? S.xw : S.xi;
+    const double* b = which == 0 ? S.xi : S.xw;
+    double acc = 0.0;
+    for (int k = 0; k < P.naug; ++k) acc = fma(a[k], b[k], acc);
+    return acc;
+  }
+
   // One pass over all tiles of this CTA; writes the CTA's partial sums.
   // Returns the number of reduction slots used.
   __device__ int run_pass(const PassT<B>& ps) {
     const DevOp& d = P.op;
     const Tiling& tl = P.tl;
     zero_acc();
+    if constexpr (AUG) aug_begin(ps);
     const bool stencil = ps.wout != nullptr;
     for (int t = grank; t < tl.ntiles; t += gsize) {
       int bx = t % tl.tiles_x;
@@ -356,6 +424,12 @@ struct Engine {
       vx = warp_sum(vx);
       vw = warp_sum(vw);
       if (c < ps.d1 && lane == 0) {
+        if constexpr (AUG) {
+          if (grank == 0) {
+            vx += aug_dot(c, S.xi);
+            vw += aug_dot(c, S.xw);
+          }
+        }
         part[c - ps.d0] = (ps.dmode & DOT_X) ? vx : 0.0;
         part[nd + c - ps.d0] = (ps.dmode & DOT_W) ? vw : 0.0;
       }
@@ -371,6 +445,9 @@ struct Engine {
     if (tid < 3) {
       double acc = 0;
       for (int i = 0; i < NW; ++i) acc += S.bred[i][tid];
+      if constexpr (AUG) {
+        if (grank == 0 && (ps.self & (1 << tid))) acc += aug_self(tid);
+      }
       part[2 * nd + tid] = acc;
     }
     return 2 * nd + 3;
@@ -492,6 +569,10 @@ struct Engine {
     }
     if (r < 0) return false;
     if (r == 1) {
+      if (AUG && tid < P.naug) {
+        if (S.aug_xcol >= 0) P.xaug[(long long)S.aug_xcol * PMAX + tid] = S.xi[tid];
+        if (S.aug_wcol >= 0) P.xaug[(long long)S.aug_wcol * PMAX + tid] = S.xw[tid];
+      }
       fn();
       __syncthreads();
       if (tid == 0) { P.ctl->barriers += 1; }
@@ -949,11 +1030,11 @@ struct Engine {
 #define LSA_MINB_F32 2
 #endif
 
-template <class Op, class Tc, class B>
+template <class Op, class Tc, class B, bool AUG = false>
 __global__ void __launch_bounds__(NT, (sizeof(Tc) == 8) ? LSA_MINB_F64 : LSA_MINB_F32)
     k_arnoldi(ArnoldiParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  using E = Engine<Op, Tc, B>;
+  using E = Engine<Op, Tc, B, AUG>;
   typename E::Smem& S = *reinterpret_cast<typename E::Smem*>(smem_raw);
   E e(P, S, reinterpret_cast<double*>(smem_raw + E::small_offset()));
   if (!e.place()) return;
@@ -983,6 +1064,9 @@ cudaError_t launch_arnoldi_t(const ArnoldiParams& P, int G, cudaStream_t s) {
   ArnoldiParams Pc = P;
   void* args[1] = {&Pc};
   auto k = k_arnoldi<Op, Tc, Tc>;
+  if constexpr (sizeof(Tc) == 8 && Op::KIND <= LSA_OP_ADR3D) {   // the three workload operators
+    if (P.naug > 0) k = k_arnoldi<Op, Tc, Tc, true>;
+  }
   size_t sm = Engine<Op, Tc, Tc>::smem_bytes();
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;

@@ -101,11 +101,18 @@ struct ArnoldiParams {
   double brk_tol;
   long long timeout_ns;
   float* E;                // streaming float32 kernel: edge array, (m+3) columns of N/8 (or null)
+  // Augmented operator of Eqs. 8-9 (phi-function linear combinations): every
+  // vector carries naug = p extra entries; Aaug [x; xi] = [A x + B xi; K xi]
+  // with B = [b_p, ..., b_1] and K the p x p upper shift.  naug = 0: plain A.
+  int naug;
+  const double* baug;      // b_0..b_p, (p+1) x N (column k of B is b_{p-k})
+  double* xaug;            // extra entries of the extended basis columns, (m+3) x PMAX
+  double aug_t;            // extra entries of the start vector: exp(aug_t K) e_p
 };
 
 // Workspace layout (all offsets 256-byte aligned).
 struct Layout {
-  size_t ctl, partials, gsum, T, L, H, V, W0, W1, small, coefs, g0, g1, E, total;
+  size_t ctl, partials, gsum, T, L, H, V, W0, W1, small, coefs, g0, g1, E, xaug, total;
   int G;                   // CTAs of the persistent Arnoldi kernel
 };
 

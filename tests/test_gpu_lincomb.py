@@ -1,0 +1,132 @@
+"""phi-function linear combinations u = sum_j tau^j phi_j(tau A) b_j through the
+CUDA path (lsa_phiv_lincomb: Krylov projection of the augmented operator of
+Eqs. 7-9 in equal sub-steps) against the oracle's projection with the same m
+and sub-steps, dense exponentials of the augmented matrix, and the plain phi
+products."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import exact as OE
+from oracle import lincomb as OL
+from oracle import operators as OP
+from tests.gpu_util import FP64_TOL, expected_syncs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def case(name, m=30):
+    if name == "advdiff2d":
+        return W.advdiff2d(48, ny=40, m=m, h=0.5, diff=0.01)        # ragged tiles in y
+    if name == "grayscott2d":
+        cfg = W.grayscott2d(32, Du=2e-3, Dv=1e-3, h=0.5, m=m, seed=105)
+        cfg.update(ny=24, name="grayscott2d_32x24")
+        return cfg
+    cfg = W.adr3d(20, m=m, h=5e-3)
+    cfg.update(ny=16, nz=12, name="adr3d_20x16x12")                    # ragged 3D tiles
+    return cfg
+
+
+def setup(cfg, p):
+    import paper_2410_14917_gb300 as lsa
+
+    inp = W.lincomb_inputs(cfg, p)
+    fields = {k: torch.from_numpy(v).cuda() for k, v in inp.items() if k not in ("v", "b")}
+    op = lsa.Operator.from_workload(cfg, fields)
+    A = OP.from_workload(cfg, inp)
+    return lsa, op, A, inp["b"], torch.from_numpy(inp["b"]).cuda().contiguous()
+
+
+def rel(a, b):
+    a = a.detach().cpu().numpy() if hasattr(a, "detach") else np.asarray(a)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("name", ["advdiff2d", "grayscott2d", "adr3d"])
+@pytest.mark.parametrize("variant", ["hcwy", "mgs"])
+@pytest.mark.parametrize("nsub", [1, 3])
+def test_lincomb_matches_oracle(name, variant, nsub):
+    p, tau = 3, 0.5 if name != "adr3d" else 5e-3
+    cfg = case(name)
+    lsa, op, A, b, bd = setup(cfg, p)
+    ref, infos = OL.lincomb_krylov(lambda x: A @ x, list(b), tau, cfg["m"], nsub, "mgs")
+    u, st = lsa.phiv_lincomb(op, bd, tau, cfg["m"], nsub, variant=variant)
+    assert st["status"] >= 0
+    assert rel(u, ref) < FP64_TOL
+    m_eff = min(i["m_eff"] for i in infos)
+    assert st["m_eff"] == m_eff
+    assert st["grid_syncs"] == nsub * expected_syncs(variant, m_eff, 0) + (st["norm_fallbacks"] if variant != "mgs" else 0)
+
+
+@pytest.mark.parametrize("variant", ["hncwy", "hgsmgs", "cgs2", "iocgs"])
+def test_lincomb_other_variants(variant):
+    p, tau = 2, 0.5
+    cfg = case("grayscott2d")
+    lsa, op, A, b, bd = setup(cfg, p)
+    ref, _ = OL.lincomb_krylov(lambda x: A @ x, list(b), tau, cfg["m"], 2,
+                               "iocgs" if variant == "iocgs" else "mgs")
+    u, st = lsa.phiv_lincomb(op, bd, tau, cfg["m"], 2, variant=variant)
+    assert rel(u, ref) < FP64_TOL
+
+
+def test_lincomb_matches_dense_augmented_exponential():
+    p, tau = 2, 1.3
+    cfg = W.advdiff2d(16, m=48, diff=0.01)
+    lsa, op, A, b, bd = setup(cfg, p)
+    ref = OE.phi_combination_dense(A.toarray(), list(b), tau, expm=OE.scipy_expm)
+    u, st = lsa.phiv_lincomb(op, bd, tau, 48, 2, variant="hcwy")
+    assert rel(u, ref) < FP64_TOL
+
+
+def test_lincomb_single_vector_is_the_phi_product():
+    p, tau = 3, 0.5
+    cfg = case("grayscott2d")
+    lsa, op, A, b, bd = setup(cfg, p)
+    z = torch.zeros_like(bd)
+    z[p] = bd[p]
+    u, _ = lsa.phiv_lincomb(op, z.contiguous(), tau, cfg["m"], 1, variant="hcwy")
+    y, _ = lsa.phiv(op, bd[p].contiguous(), tau, p, cfg["m"], variant="hcwy")
+    yp = (tau ** p) * y[p]
+    assert rel(u, yp.cpu().numpy()) < 1e-11
+
+
+def test_lincomb_p0_is_phiv_bit_for_bit():
+    cfg = case("advdiff2d")
+    lsa, op, A, b, bd = setup(cfg, 0)
+    u, _ = lsa.phiv_lincomb(op, bd, 0.5, cfg["m"], 1, variant="hcwy")
+    y, _ = lsa.phiv(op, bd[0].contiguous(), 0.5, 0, cfg["m"], variant="hcwy")
+    assert torch.equal(u, y[0])
+
+
+def test_lincomb_tau_zero_returns_b0():
+    cfg = case("advdiff2d")
+    lsa, op, A, b, bd = setup(cfg, 2)
+    u, _ = lsa.phiv_lincomb(op, bd, 0.0, cfg["m"], 2, variant="hcwy")
+    assert rel(u, b[0]) < 1e-14
+
+
+def test_lincomb_in_place_on_b0():
+    p, tau = 2, 0.5
+    cfg = case("grayscott2d")
+    lsa, op, A, b, bd = setup(cfg, p)
+    ref, _ = OL.lincomb_krylov(lambda x: A @ x, list(b), tau, cfg["m"], 2, "mgs")
+    u, _ = lsa.phiv_lincomb(op, bd, tau, cfg["m"], 2, variant="hcwy", u=bd[0])
+    assert rel(bd[0], ref) < FP64_TOL
+
+
+def test_lincomb_rejects_bad_arguments():
+    import paper_2410_14917_gb300 as lsa
+    from paper_2410_14917_gb300 import _binding as B
+
+    cfg = case("advdiff2d")
+    _, op, _, _, bd = setup(cfg, 1)
+    u = torch.empty(bd.shape[1], dtype=torch.float64, device="cuda")
+    work = lsa.Workspace.for_call(op, 30, 0, "fp64")
+    lib = B.lib()
+    import ctypes
+    args = lambda nsub, prec: (ctypes.byref(op.c), ctypes.c_void_p(bd.data_ptr()), 1, 0.5, nsub, 30, 0.0,
+                               B.VARIANTS["hcwy"], prec, ctypes.c_void_p(u.data_ptr()),
+                               ctypes.c_void_p(work.ptr), work.nbytes, None, None)
+    assert lib.lsa_phiv_lincomb(*args(0, B.PRECISIONS["fp64"])) == B.LSA_ERR_ARG
+    assert lib.lsa_phiv_lincomb(*args(1, B.PRECISIONS["fp32"])) == B.LSA_ERR_ARG

@@ -58,6 +58,7 @@ def test_host_only_calls(lib):
     gs = LsaOp(2, 8, 8, 1, 0.1, 1e-3, 1e-3, (ctypes.c_double * 3)(), 0.04, 0.06, None, None)
     assert lib.lsa_op_dof(ctypes.byref(gs)) == -1           # Gray-Scott without its fields
     assert lib.lsa_phiv(None, None, 0.0, 0, 1, 0.0, 0, 0, None, None, 0, None, None) == -1
+    assert lib.lsa_phiv_lincomb(None, None, 0, 0.0, 1, 1, 0.0, 0, 0, None, None, 0, None, None) == -1
 
 
 def test_library_targets_sm103a():

@@ -121,6 +121,17 @@ def adjoint_inputs(cfg: dict) -> dict:
     return out
 
 
+def lincomb_inputs(cfg: dict, p: int) -> dict:
+    """Inputs of a phi-function linear combination sum_j tau^j phi_j(tau A) b_j:
+    those of ``make_inputs`` (the operator's fields) and the vectors
+    b_0..b_p ~ U[-1,1]^N as a (p+1, N) array from a second generator seeded
+    with the configuration's seed + 7919."""
+    out = make_inputs(cfg)
+    rng = np.random.default_rng(cfg["seed"] + 7919)
+    out["b"] = rng.uniform(-1.0, 1.0, (p + 1, n_dof(cfg)))
+    return out
+
+
 # ---------------------------------------------------------------------------
 # Batched workload: 512 independent 2D advection-diffusion instances.
 
