@@ -19,6 +19,8 @@ Modules (each function cites the passage of the paper it follows):
              with the phi augmentation of Sect. 2.1)
   lincomb    sum_j tau^j phi_j(tau A) b_j by Krylov projection of the
              augmented operator (Sect. 2.1, Eqs. 7-9) in equal sub-steps
+  adjoint    gradients of a phi_1 loss (Krylov and dense Frechet forms)
+  integrators  SRERK3, EPI4 and EPI5 (Sect. 4) on phi linear combinations
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test
 against a closed form, a library routine, brute force or a worked example of

@@ -20,6 +20,7 @@ from oracle import arnoldi as OA
 from oracle import exact as OE
 from oracle import expm as OX
 from oracle import krylov as OK
+from oracle import integrators as OI
 from oracle import lincomb as OL
 from oracle import operators as OP
 from oracle import phi as OPHI
@@ -484,3 +485,59 @@ def pin_lincomb_single_vector(p=3, tau=0.9):
     u0, _ = OL.lincomb_krylov(lambda x: A @ x, [bs[0]], tau, N, 1)
     ref0 = scipy.linalg.expm(tau * A) @ bs[0]
     return max(err, float(np.abs(u0 - ref0).max() / np.abs(ref0).max()))
+
+
+# ---------------------------------------------------------------------------
+# Exponential integrators of Sect. 4 (SRERK3, EPI4, EPI5).
+
+def pin_integrators_linear_exact(h=0.1, nsteps=6):
+    """u' = A u: the remainder R vanishes and every method steps exactly with
+    exp(hA), so nsteps steps equal exp(nsteps h A) u_0 (scipy)."""
+    cfg = W.advdiff2d(6, diff=0.05, vel=(1.0, 0.5))
+    A = OP.from_workload(cfg, {}).toarray()
+    u0 = np.random.default_rng(31).uniform(-1, 1, A.shape[0])
+    F, Jf = OI.linear_problem(A)
+    ref = scipy.linalg.expm(nsteps * h * A) @ u0
+    err = 0.0
+    for meth in ("srerk3", "epi4", "epi5"):
+        u = OI.integrate(meth, F, Jf, u0, h, nsteps, OI.dense_lincomb)
+        err = max(err, float(np.abs(u - ref).max() / np.abs(ref).max()))
+    return err
+
+
+_ORDER_CACHE = {}
+
+
+def integrator_orders(T=1.0, steps=(8, 16, 32)):
+    """Observed convergence orders on a 6 x 6 Gray-Scott system (Radau
+    reference at rtol 1e-13); the multistep methods start from reference
+    values, so the order is the method's own.  Returns {method: order of the
+    last halving}."""
+    import scipy.integrate as si
+
+    key = (T, steps)
+    if key in _ORDER_CACHE:
+        return _ORDER_CACHE[key]
+    cfg = W.grayscott2d(6, Du=2e-2, Dv=1e-2)
+    inp = W.make_inputs(cfg)
+    u0 = np.concatenate([inp["u0"], inp["v0"]])
+    F, Jf = OI.grayscott_problem(cfg)
+    ref = si.solve_ivp(lambda t, y: F(y), (0, T), u0, method="Radau", rtol=1e-13, atol=1e-13,
+                       jac=lambda t, y: Jf(y).toarray(), dense_output=True)
+    uT = ref.y[:, -1]
+    out = {}
+    for meth in ("srerk3", "epi4", "epi5"):
+        errs = []
+        for nst in steps:
+            h = T / nst
+            if meth == "srerk3":
+                u = OI.integrate(meth, F, Jf, u0, h, nst, OI.dense_lincomb)
+            else:
+                P = OI.EPI_ALPHA[int(meth[3:])].shape[1]
+                hist = [ref.sol(i * h) for i in range(P, -1, -1)]
+                u = OI.integrate(meth, F, Jf, hist[0], h, nst - P, OI.dense_lincomb, history=hist[1:])
+            errs.append(float(np.abs(u - uT).max()))
+        out[meth] = math.log2(errs[-2] / errs[-1])
+    _ORDER_CACHE.clear()
+    _ORDER_CACHE[key] = out
+    return out

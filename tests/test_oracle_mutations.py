@@ -139,3 +139,31 @@ def test_lincomb_reversed_forcing_columns_are_caught(monkeypatch):
     monkeypatch.setattr(OL, "aug_matvec", lambda mv, bs: orig(mv, [bs[0]] + list(bs[1:])[::-1]))
     assert pins.pin_lincomb_solves_forced_ode() > 1e-3
     assert pins.pin_lincomb_diagonal() > 1e-3
+
+
+def test_epi_coefficient_slip_is_caught(monkeypatch):
+    from oracle import integrators as OI
+    bad = OI.EPI_ALPHA[4].copy()
+    bad[1, 0] *= 1.1
+    monkeypatch.setitem(OI.EPI_ALPHA, 4, bad)
+    pins._ORDER_CACHE.clear()
+    try:
+        assert pins.integrator_orders()["epi4"] < 3.5
+    finally:
+        pins._ORDER_CACHE.clear()
+
+
+def test_srerk3_weight_slip_is_caught(monkeypatch):
+    from oracle import integrators as OI
+    orig = OI._combo
+
+    def bad(lincomb, J, cs, h):
+        if len(cs) == 4 and cs[3] is not None:
+            cs = cs[:3] + [cs[3] * (3.0 / (32.0 / 9.0))]        # 3 instead of 32/9
+        return orig(lincomb, J, cs, h)
+    monkeypatch.setattr(OI, "_combo", bad)
+    pins._ORDER_CACHE.clear()
+    try:
+        assert pins.integrator_orders()["srerk3"] < 2.5
+    finally:
+        pins._ORDER_CACHE.clear()
