@@ -201,6 +201,18 @@ lsa_status lsa_phiv_lincomb(const lsa_op* op, const double* b, int p, double tau
                             double tol, int variant, int precision, double* u, void* work,
                             size_t work_bytes, lsa_stats* stats, void* stream);
 
+/* Exponential-integrator building blocks (Sect. 4) besides the phi products.
+ * lsa_rhs: f = F(u) for the Gray-Scott system whose Jacobian at a state is
+ *   the LSA_OP_GRAYSCOTT2D operator: F(u, v) = [Du Lap u - u v^2 + F (1 - u);
+ *   Dv Lap v + u v^2 - (F + k) v], periodic 5-point Laplacian with spacing dx.
+ *   op: that operator's descriptor (its fields are not read).  u, f: dev,
+ *   2*nx*ny doubles, species-major; must not overlap.  LSA_ERR_ARG for other
+ *   operator kinds.
+ * lsa_axpby: w = a x + b y over n doubles (dev); w may be x or y. */
+lsa_status lsa_rhs(const lsa_op* op, const double* u, double* f, void* stream);
+lsa_status lsa_axpby(long long n, double a, const double* x, double b, const double* y, double* w,
+                     void* stream);
+
 /* S5 alone: coefficients C (dev, (p+2) x m doubles, row k = phi_k(h H_m) e_1,
  * k = 0..p+1) from one exponential of the augmented (m+p+1)-sized matrix,
  * computed on the GPU.  H: dev, column-major with leading dimension ldh >= m. */

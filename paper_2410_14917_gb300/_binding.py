@@ -54,6 +54,8 @@ SIGNATURES = {
     "lsa_phiv_lincomb": (c_int, [POINTER(LsaOp), c_void_p, c_int, c_double, c_int, c_int, c_double,
                                  c_int, c_int, c_void_p, c_void_p, c_size_t, POINTER(LsaStats),
                                  c_void_p]),
+    "lsa_rhs": (c_int, [POINTER(LsaOp), c_void_p, c_void_p, c_void_p]),
+    "lsa_axpby": (c_int, [c_longlong, c_double, c_void_p, c_double, c_void_p, c_void_p, c_void_p]),
     "lsa_expm_phi": (c_int, [c_void_p, c_int, c_int, c_double, c_int, c_void_p, c_void_p, c_size_t,
                              c_void_p]),
     "lsa_read_stats": (c_int, [c_void_p, POINTER(LsaStats), c_void_p]),

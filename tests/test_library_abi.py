@@ -59,6 +59,9 @@ def test_host_only_calls(lib):
     assert lib.lsa_op_dof(ctypes.byref(gs)) == -1           # Gray-Scott without its fields
     assert lib.lsa_phiv(None, None, 0.0, 0, 1, 0.0, 0, 0, None, None, 0, None, None) == -1
     assert lib.lsa_phiv_lincomb(None, None, 0, 0.0, 1, 1, 0.0, 0, 0, None, None, 0, None, None) == -1
+    assert lib.lsa_rhs(ctypes.byref(op), None, None, None) == -1        # not a Gray-Scott operator
+    assert lib.lsa_axpby(-1, 1.0, None, 1.0, None, None, None) == -1
+    assert lib.lsa_axpby(0, 1.0, None, 1.0, None, None, None) == 0      # nothing to do
 
 
 def test_library_targets_sm103a():
