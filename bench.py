@@ -6,7 +6,11 @@
 --config 3 selects the batched workload (512 advection-diffusion instances of
 uneven size in one persistent launch per step); --config 4 the adjoint workload
 (a step is one loss-and-gradient evaluation of 1/2 ||phi_1(hA(theta))v - y_t||^2
-on the 256x256 Gray-Scott Jacobian: the forward phi product and lsa_phiv_vjp).
+on the 256x256 Gray-Scott Jacobian: the forward phi product and lsa_phiv_vjp);
+--config 5 the exponential-integrator workload (a step is one EPI4 time step,
+Sect. 4, of the Gray-Scott system on the 512x512 grid: one phi-function linear
+combination of the augmented operator plus the remainder evaluations), timed
+beside the same run with the ioCGS baseline (the paper's runtime ratio).
 
 A step is one phiv call -- the whole hot path (stencil matvecs, grouped
 reductions, correction, projection, small exponential, output combination) over
@@ -188,6 +192,9 @@ def run_reference(args, world, rank):
     from oracle import krylov as OK
     from oracle import operators as OP
 
+    if args.config == 5:
+        run_reference_integrator(args, world, integrator_workload(args.size))
+        return
     cfg = workload(args.config, args.size)
     if cfg.get("kind") == "batched":
         run_reference_batched(args, world, cfg)
@@ -598,6 +605,166 @@ def bench_adjoint(args, world, rank, local, cfg):
         torch.distributed.destroy_process_group()
 
 
+def integrator_workload(size=0):
+    import workloads as W
+
+    cfg = W.grayscott2d(size or 512, h=1.0, m=64, p=3)
+    cfg.update(name=f"grayscott2d_{cfg['nx']}_epi4", method="epi4", nsub=1)
+    return cfg
+
+
+def bench_integrator(args, world, rank, local, cfg):
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2410_14917_gb300.integrators import GrayScottIntegrator
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    inp = W.make_inputs(cfg)
+    N = W.n_dof(cfg)
+    u0 = torch.from_numpy(np.concatenate([inp["u0"], inp["v0"]])).to(dev)
+    h, m, method = cfg["h"], cfg["m"], cfg["method"]
+    stream = torch.cuda.current_stream()
+    flush = None if args.no_flush else torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def make(variant):
+        it = GrayScottIntegrator(cfg["nx"], cfg["ny"], cfg["dx"], cfg["diff"], cfg["diff2"], cfg["F"],
+                                 cfg["k"], u0, m=m, nsub=cfg["nsub"], variant=variant)
+        it.run(method, h, 2)                   # the SRERK3 start: EPI4 needs u_{n-1}, u_{n-2}
+        s0 = it.stats["grid_syncs"]
+        it.run(method, h, 1)                   # one EPI4 step with statistics
+        it.syncs_per_step = it.stats["grid_syncs"] - s0
+        it.collect_stats = False
+        for _ in range(args.warmup):
+            it.run(method, h, 1)
+        return it
+
+    def timed(it, steps):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        torch.cuda.synchronize()
+        l0 = it.stats["launches"]
+        for i in range(steps):
+            if flush is not None:
+                flush.fill_(i & 0xFF)
+            ev[i][0].record(stream)
+            it.run(method, h, 1)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in ev], it.stats["launches"] - l0
+
+    it = make(args.variant)
+    syncs_step = it.syncs_per_step
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms, launches = timed(it, args.steps)
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    tot_ms, value = aggregate_replicas(sum(step_ms), args.steps, world, dev)
+    ms_step = tot_ms / args.steps
+
+    # the paper's metric: the integrator with this variant over the same run with ioCGS
+    io = make("iocgs")
+    io_syncs = io.syncs_per_step
+    io_ms = statistics.mean(timed(io, args.steps)[0])
+
+    # end to end: the state from pinned host memory, one step, the state back
+    s_host = u0.cpu().pin_memory()
+    s_back = torch.empty(N, dtype=torch.float64).pin_memory()
+    e2e_steps = max(3, min(args.steps, 10))
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        it.u.copy_(s_host, non_blocking=True)
+        it.run(method, h, 1)
+        s_back.copy_(it.u, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_value = e2e_steps / (e0.elapsed_time(e1) / 1e3) * world
+
+    byts, flops = algorithmic_counts(cfg, "fp64", m)
+    achieved = flops / (ms_step / 1e3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+            "kernel": "whole EPI4 step (augmented-operator k_arnoldi with its small kernels)",
+            "peak_source": "FP64 FMA pipe from unit counts and max clock (152 SMs x 2 FMA/clk x 2.07 GHz)",
+            "algorithmic_flops": flops}
+    line = {"metric": METRIC, "value": value, "unit": "integrator steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": cfg["name"], "N": N, "method": method, "h": h, "m": m,
+                       "nsub": cfg["nsub"], "variant": args.variant, "precision": "fp64",
+                       "l2": "flushed between timed steps (256 MiB write)" if flush is not None
+                       else "not flushed", "parallelism": f"replicas x{world}"},
+            "lincomb_per_step": 1,
+            "grid_syncs_per_step": syncs_step,
+            "vs_iocgs": {"ms_iocgs": io_ms, "ms_variant": ms_step, "ratio": ms_step / io_ms,
+                         "grid_syncs_iocgs": io_syncs,
+                         "note": "integrator runtime with this variant / with ioCGS (Sect. 4's ratio)"},
+            "roofline": roof,
+            "e2e": {"value": e2e_value, "unit": "integrator steps/s", "h2d_bytes_per_step": N * 8,
+                    "d2h_bytes_per_step": N * 8},
+            "gpu_launches": launches,
+            "clocks": clocks}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        el, sample = oracle_integrator_sample(cfg, args.variant)
+        line["cpu_baseline"] = {"value": 1.0 / el, "unit": "integrator steps/s", "cores": os.cpu_count(),
+                                "kind": "oracle", "sample": sample}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def oracle_integrator_sample(cfg, variant):
+    """One EPI4 step of the oracle (float64 NumPy/SciPy, Krylov combinations
+    with the same m) from the workload's state, the history given."""
+    import numpy as np
+
+    import workloads as W
+    from oracle import integrators as OI
+
+    inp = W.make_inputs(cfg)
+    u0 = np.concatenate([inp["u0"], inp["v0"]])
+    F, Jf = OI.grayscott_problem(cfg)
+    lc = OI.krylov_lincomb(cfg["m"], cfg["nsub"], variant)
+    t0 = time.perf_counter()
+    OI.epi_step(4, F, Jf, [u0, u0, u0], cfg["h"], lc)
+    el = time.perf_counter() - t0
+    return el, f"one EPI4 step of {cfg['name']} (history given, {variant} Krylov, float64 NumPy/SciPy)"
+
+
+def run_reference_integrator(args, world, cfg):
+    t_all = []
+    t0 = time.perf_counter()
+    while len(t_all) < max(1, args.steps):
+        el, sample = oracle_integrator_sample(cfg, args.variant)
+        t_all.append(el)
+        if time.perf_counter() - t0 > 3 * args.cpu_budget:
+            break
+    n, el = len(t_all), sum(t_all)
+    value = n / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "integrator steps/s",
+            "n_gpus": world, "steps": n, "warmup": 0, "ms_per_step": 1e3 * el / n,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": cfg["name"], "method": cfg["method"], "h": cfg["h"],
+                                             "m": cfg["m"], "variant": args.variant, "precision": "fp64"},
+            "cpu_baseline": {"value": value, "unit": "integrator steps/s", "cores": os.cpu_count(),
+                             "kind": "oracle", "sample": f"{n} x " + sample},
+            "e2e": {"value": value, "unit": "integrator steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def cpu_baseline(cfg, variant, budget):
     """Time the oracle (as it stands) on a bounded sample: whole phiv calls on
     the full workload until ~budget seconds have passed.  Also returns the last
@@ -633,6 +800,9 @@ def main():
     import paper_2410_14917_gb300 as lsa
     import workloads as W
 
+    if args.config == 5:
+        bench_integrator(args, world, rank, local, integrator_workload(args.size))
+        return
     cfg = workload(args.config, args.size)
     if cfg.get("kind") == "batched":
         bench_batched(args, world, rank, local, cfg)

@@ -43,7 +43,7 @@ class GrayScottIntegrator:
     sub-steps, Gram-Schmidt variant)."""
 
     def __init__(self, nx, ny, dx, Du, Dv, F, k, state: torch.Tensor, m=30, nsub=1,
-                 variant="hcwy", tol=0.0, stream=None):
+                 variant="hcwy", tol=0.0, stream=None, collect_stats=True):
         if state.dtype != torch.float64 or not state.is_cuda or state.numel() != 2 * nx * ny:
             raise ValueError("state must be a float64 CUDA tensor of 2*nx*ny entries")
         self.n = nx * ny
@@ -56,7 +56,8 @@ class GrayScottIntegrator:
         self.work_lc = Workspace.for_call(self.op, min(m, self.N + 4), 0)
         self.work_mv = Workspace.for_call(self.op, 1, 0)
         self.hist = []          # u_{n-1}, u_{n-2}, ... of the multistep methods
-        self.stats = dict(lincomb_calls=0, grid_syncs=0, steps=0)
+        self.collect_stats = collect_stats    # False: no per-call synchronisation
+        self.stats = dict(lincomb_calls=0, grid_syncs=0, steps=0, launches=0)
         dev = self.u.device
         self._b = torch.empty((5, self.N), dtype=torch.float64, device=dev)
         self._t = [torch.empty(self.N, dtype=torch.float64, device=dev) for _ in range(4)]
@@ -64,16 +65,19 @@ class GrayScottIntegrator:
 
     # -- kernels ------------------------------------------------------------
     def rhs(self, w, out):
+        self.stats["launches"] += 1
         _check(B.lib().lsa_rhs(ctypes.byref(self.op.c), _ptr(w), _ptr(out), _stream_ptr(self.stream)),
                "lsa_rhs", ok=(B.LSA_OK,))
         return out
 
     def axpby(self, a, x, b, y, out):
+        self.stats["launches"] += 1
         _check(B.lib().lsa_axpby(self.N, float(a), _ptr(x), float(b), _ptr(y), _ptr(out),
                                  _stream_ptr(self.stream)), "lsa_axpby", ok=(B.LSA_OK,))
         return out
 
     def jv(self, x, out):
+        self.stats["launches"] += 2          # operator set-up and the stencil
         _check(B.lib().lsa_matvec(ctypes.byref(self.op.c), _ptr(x), _ptr(out), B.PRECISIONS["fp64"],
                                   ctypes.c_void_p(self.work_mv.ptr), self.work_mv.nbytes,
                                   _stream_ptr(self.stream)), "lsa_matvec", ok=(B.LSA_OK,))
@@ -99,9 +103,11 @@ class GrayScottIntegrator:
             for coef, vec in terms:
                 self.axpby(1.0, b[k], coef / h ** k, vec, b[k])
         _, st = phiv_lincomb(self.op, b, h, self.m, self.nsub, self.tol, self.variant, u=out,
-                             work=self.work_lc, stream=self.stream)
+                             work=self.work_lc, stream=self.stream, stats=self.collect_stats)
         self.stats["lincomb_calls"] += 1
-        self.stats["grid_syncs"] += st["grid_syncs"]
+        self.stats["launches"] += 4 * self.nsub
+        if st is not None:
+            self.stats["grid_syncs"] += st["grid_syncs"]
         return out
 
     # -- methods ------------------------------------------------------------
