@@ -42,6 +42,10 @@ PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 # FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (recipe's unit counts and clock)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# DRAM bytes (read + write) of one launch of the dominant kernel from an ncu
+# capture of the current kernel (profiles/k_arnoldi_grayscott2d_512_fp64.md);
+# a workload without an up-to-date capture reports null.
+PROFILED_TRAFFIC = {("grayscott2d_512", "fp64", "hcwy"): 9.516027e9 + 0.801385e9}
 
 
 def parse():
@@ -907,7 +911,8 @@ def main():
     if args.precision == "fp64":
         achieved = flops / (ms_a / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "frac": achieved / FP64_PEAK_TFLOPS,
+                "traffic": PROFILED_TRAFFIC.get((cfg["name"], args.precision, args.variant)),
                 "kernel": "k_arnoldi (persistent hybrid Arnoldi)",
                 "peak_source": "FP64 FMA pipe from unit counts and max clock (152 SMs x 2 FMA/clk x 2.07 GHz)",
                 "hbm_gbs": byts / (ms_a / 1e3) / 1e9, "hbm_frac": byts / (ms_a / 1e3) / 1e9 / hbm_peak,
