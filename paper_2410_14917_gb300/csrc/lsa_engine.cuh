@@ -575,7 +575,7 @@ struct Engine {
       }
       fn();
       __syncthreads();
-      if (tid == 0) { P.ctl->barriers += 1; }
+      if (tid == 0) { P.ctl->barriers = __ldcg(&P.ctl->barriers) + 1; }
       barrier_release(br, gen);
     }
     ++gen;
@@ -615,9 +615,9 @@ struct Engine {
         if (j == 1) {
           ctl->beta = sqrt(Gj);
         } else {
-          double tn = ctl->nrm_est * sqrt(Gj);   // true norm of the previous vector
+          double tn = __ldcg(&ctl->nrm_est) * sqrt(Gj);   // true norm of the previous vector
           S.true_nrm = tn;
-          if (!(tn > P.brk_tol * ctl->aw_prev)) { // lagged breakdown test
+          if (!(tn > P.brk_tol * __ldcg(&ctl->aw_prev))) { // lagged breakdown test
             Hat(j - 1, j - 2) = tn;
             ctl->m_eff = j - 1;
             ctl->breakdown = 1;
@@ -629,7 +629,7 @@ struct Engine {
         temp2[np] = sj * sj * Pj;
         temp2[np + 1] = sj * sj * Q;
       }
-      ctl->syncs += 1;
+      ctl->syncs = __ldcg(&ctl->syncs) + 1;
     }
     __syncthreads();
     if (S.flag) return;
@@ -697,7 +697,7 @@ struct Engine {
       double awn = sqrt(t);
       S.scale = 1.0;
       if (t < S.ss) {                         // Pythagorean radicand negative: explicit norm
-        ctl->fallbacks += 1;
+        ctl->fallbacks = __ldcg(&ctl->fallbacks) + 1;
         ctl->fallback_pending = 1;
         ctl->nrm_est = 1.0;
       } else {
@@ -713,7 +713,7 @@ struct Engine {
       }
       ctl->aw_prev = awn;
       ctl->a = S.sj * S.scale;
-      if (j == P.m && !ctl->done) ctl->m_eff = P.m;
+      if (j == P.m && !__ldcg(&ctl->done)) ctl->m_eff = P.m;
     }
     __syncthreads();
     for (int i = tid; i < j; i += NT) {
@@ -746,8 +746,8 @@ struct Engine {
     Ctl* ctl = P.ctl;
     if (tid == 0) {
       double nrm = sqrt(S.red[0]);
-      ctl->syncs += 1;
-      if (!(nrm > P.brk_tol * ctl->aw_prev)) {
+      ctl->syncs = __ldcg(&ctl->syncs) + 1;
+      if (!(nrm > P.brk_tol * __ldcg(&ctl->aw_prev))) {
         Hat(j, j - 1) = nrm;
         ctl->m_eff = j;
         ctl->breakdown = 1;
@@ -767,12 +767,12 @@ struct Engine {
     if (tid == 0) {
       const int m = P.m;
       double nrm = sqrt(S.red[0]);
-      double hl = ctl->nrm_est * nrm;       // true norm of the projected v_{m+1}
+      double hl = __ldcg(&ctl->nrm_est) * nrm;       // true norm of the projected v_{m+1}
       Hat(m, m - 1) = hl;
       ctl->h_last = hl;
       ctl->sigma[m] = (nrm > 0.0) ? 1.0 / nrm : 0.0;
-      ctl->syncs += 1;
-      if (!(hl > P.brk_tol * ctl->aw_prev)) ctl->breakdown = 1;
+      ctl->syncs = __ldcg(&ctl->syncs) + 1;
+      if (!(hl > P.brk_tol * __ldcg(&ctl->aw_prev))) ctl->breakdown = 1;
     }
   }
 
@@ -836,7 +836,7 @@ struct Engine {
       if (tid == 0) {
         double b = sqrt(S.red[0]);
         P.ctl->beta = b;
-        P.ctl->syncs += 1;
+        P.ctl->syncs = __ldcg(&P.ctl->syncs) + 1;
         if (b == 0.0) { P.ctl->done = 1; P.ctl->m_eff = 0; }     // zero start vector: y = 0
         else if (!isfinite(b)) { P.ctl->done = 1; P.ctl->status = (int)LSA_ERR_NUMERIC; }
         P.ctl->a = (b > 0.0) ? 1.0 / b : 0.0;
@@ -881,7 +881,7 @@ struct Engine {
               Hat(0, j - 1) = h;
               P.ctl->coef[0] = h;
               P.ctl->aw_prev = sqrt(S.red[2 * nd + 2]);
-              P.ctl->syncs += 1;
+              P.ctl->syncs = __ldcg(&P.ctl->syncs) + 1;
             }
           })) return;
       for (int i = 1; i < j; ++i) {
@@ -896,7 +896,7 @@ struct Engine {
                 double h = S.red[0];
                 Hat(i, j - 1) = h;
                 P.ctl->coef[i] = h;
-                P.ctl->syncs += 1;
+                P.ctl->syncs = __ldcg(&P.ctl->syncs) + 1;
               }
             })) return;
       }
@@ -916,8 +916,8 @@ struct Engine {
       Ctl* ctl = P.ctl;
       double nrm = sqrt(S.red[0]);
       Hat(j, j - 1) = nrm;
-      ctl->syncs += 1;
-      if (!(nrm > P.brk_tol * ctl->aw_prev)) {
+      ctl->syncs = __ldcg(&ctl->syncs) + 1;
+      if (!(nrm > P.brk_tol * __ldcg(&ctl->aw_prev))) {
         ctl->m_eff = j;
         ctl->breakdown = 1;
         ctl->done = 1;
@@ -925,7 +925,7 @@ struct Engine {
       if (!isfinite(nrm)) { ctl->status = (int)LSA_ERR_NUMERIC; ctl->done = 1; ctl->m_eff = j - 1; }
       ctl->a = (nrm > 0.0) ? 1.0 / nrm : 0.0;
       ctl->h_last = nrm;
-      if (j == P.m && !ctl->done) ctl->m_eff = P.m;
+      if (j == P.m && !__ldcg(&ctl->done)) ctl->m_eff = P.m;
     }
   }
 
@@ -955,7 +955,7 @@ struct Engine {
               P.ctl->hcol[i] = h;
               P.ctl->coef[i] = h;
             }
-            if (tid == 0) { P.ctl->aw_prev = sqrt(S.red[2 * nd + 2]); P.ctl->syncs += 1; }
+            if (tid == 0) { P.ctl->aw_prev = sqrt(S.red[2 * nd + 2]); P.ctl->syncs = __ldcg(&P.ctl->syncs) + 1; }
           })) return;
       PassT<B> pb;
       pb.c0 = 0; pb.c1 = j; pb.a = 1.0; pb.src64 = nullptr; pb.srcB = w;
@@ -967,7 +967,7 @@ struct Engine {
               Hat(i, j - 1) = __ldcg(&P.ctl->hcol[i]) + h2;
               P.ctl->coef[i] = h2;
             }
-            if (tid == 0) P.ctl->syncs += 1;
+            if (tid == 0) P.ctl->syncs = __ldcg(&P.ctl->syncs) + 1;
           })) return;
       PassT<B> pc;
       pc.c0 = 0; pc.c1 = j; pc.a = 1.0; pc.src64 = nullptr; pc.srcB = w;
@@ -1009,7 +1009,7 @@ struct Engine {
               Hat(i, j - 1) = h;
               P.ctl->coef[i] = h;
             }
-            if (tid == 0) { P.ctl->aw_prev = sqrt(S.red[2 * nd + 2]); P.ctl->syncs += 1; }
+            if (tid == 0) { P.ctl->aw_prev = sqrt(S.red[2 * nd + 2]); P.ctl->syncs = __ldcg(&P.ctl->syncs) + 1; }
           })) return;
       // w -= H_{lo..j,j} v_{lo..j}; ||w||
       PassT<B> pc;

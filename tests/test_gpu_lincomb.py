@@ -130,3 +130,27 @@ def test_lincomb_rejects_bad_arguments():
                                ctypes.c_void_p(work.ptr), work.nbytes, None, None)
     assert lib.lsa_phiv_lincomb(*args(0, B.PRECISIONS["fp64"])) == B.LSA_ERR_ARG
     assert lib.lsa_phiv_lincomb(*args(1, B.PRECISIONS["fp32"])) == B.LSA_ERR_ARG
+
+
+def test_lincomb_zero_operator_closed_form():
+    # A = 0: sum_j tau^j phi_j(0) b_j = sum_j tau^j / j! b_j; the Krylov process breaks
+    # down inside the augmented space (dimension p + 1), exactly
+    import math
+
+    p, tau = 8, 0.7
+    cfg = W.advdiff2d(32, diff=0.0, vel=(0.0, 0.0), m=64)
+    lsa, op, A, b, bd = setup(cfg, p)
+    ref = sum(tau ** j / math.factorial(j) * b[j] for j in range(p + 1))
+    for variant in ("hcwy", "mgs"):
+        u, st = lsa.phiv_lincomb(op, bd, tau, 64, 3, variant=variant)
+        assert rel(u, ref) < 1e-13
+        assert st["breakdown"] == 1 and st["m_eff"] <= p + 1
+
+
+def test_lincomb_largest_p_and_m():
+    p, tau = 8, 0.5
+    cfg = case("grayscott2d", m=64)
+    lsa, op, A, b, bd = setup(cfg, p)
+    ref, _ = OL.lincomb_krylov(lambda x: A @ x, list(b), tau, 64, 1, "mgs")
+    u, st = lsa.phiv_lincomb(op, bd, tau, 64, 1, variant="hcwy")
+    assert rel(u, ref) < FP64_TOL
