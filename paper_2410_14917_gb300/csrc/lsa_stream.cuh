@@ -108,7 +108,8 @@ struct StreamLayout {
   static __host__ __device__ constexpr size_t ring_off() { return (sizeof(typename E::Smem) + 127) & ~(size_t)127; }
   static __host__ __device__ constexpr size_t bar_off() { return ring_off() + (size_t)SQ_NRING * SQ_RS * 4; }
   static __host__ __device__ constexpr size_t tab_off() { return (bar_off() + 8 * SQ_NSTMAX + 15) & ~(size_t)15; }
-  static __host__ __device__ constexpr size_t stage_off() { return (tab_off() + 16 * 3 * NW * 2 + 127) & ~(size_t)127; }
+  static __host__ __device__ constexpr size_t c2_off() { return (tab_off() + 16 * 3 * NW * 2 + 15) & ~(size_t)15; }
+  static __host__ __device__ constexpr size_t stage_off() { return (c2_off() + 8 * (MMAX + 4) + 127) & ~(size_t)127; }
 };
 
 template <class Op>
@@ -127,6 +128,7 @@ struct StreamEngine {
   unsigned pend = 0;        // thread 0: stages with copies not yet waited for
   int* s_stop;              // shared stop flag of this CTA
   int4* itab;               // per pass: each warp's boxes per task kind (see build_issue_table)
+  const unsigned long long* coef2;   // per pass: {-coef_c, -coef_c} pairs (0 past n) for the packed FMAs
 
   // per pass
   int n = 0, kn = 0, nst = 2, depth = 1, lag = 0, tpt = 1, ntask = 0, sbytes = 0;
@@ -136,8 +138,9 @@ struct StreamEngine {
   const int q, g, ly, lx4;
 
   __device__ StreamEngine(E& en, const StreamMaps& m, const StreamParams& p, float* rg,
-                          unsigned char* st, unsigned b, int* stop, int4* tab)
-      : e(en), maps(m), sp(p), ring(rg), stages(st), full0(b), s_stop(stop), itab(tab),
+                          unsigned char* st, unsigned b, int* stop, int4* tab,
+                          const unsigned long long* c2)
+      : e(en), maps(m), sp(p), ring(rg), stages(st), full0(b), s_stop(stop), itab(tab), coef2(c2),
         q(en.warp * 8 + (en.lane & 7)), g(en.lane >> 3), ly(q >> 2), lx4((q & 3) * 4) {}
 
   __device__ __forceinline__ const float* stage(int s) const {
@@ -344,6 +347,32 @@ struct StreamEngine {
   __device__ __forceinline__ static float4 lds4(const float* p) {
     return *reinterpret_cast<const float4*>(p);
   }
+  // Packed float32 pairs (fma/mul.rn.f32x2: two IEEE float32 operations per
+  // instruction, each rounded as the scalar one).
+  __device__ __forceinline__ static unsigned long long ffma2(unsigned long long a, unsigned long long b,
+                                                            unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+  }
+  __device__ __forceinline__ static unsigned long long fmul2(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+  }
+  __device__ __forceinline__ static unsigned long long pack2(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+  }
+  __device__ __forceinline__ static float2 unpack2(unsigned long long r) {
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+    return v;
+  }
+  __device__ __forceinline__ static ulonglong2 lds2x2(const float* p) {
+    return *reinterpret_cast<const ulonglong2*>(p);
+  }
   __device__ __forceinline__ static float bfly(float v) {
     v += __shfl_xor_sync(0xffffffffu, v, 8);
     v += __shfl_xor_sync(0xffffffffu, v, 16);
@@ -372,24 +401,25 @@ struct StreamEngine {
   // and then reads the source slot with a zero coefficient.
   template <int KN, int CS>
   __device__ __forceinline__ float4 proj_quad(const float* p, float a) const {
-    const float* coef = e.S.coefc + g;
+    const unsigned long long* coef = coef2 + g;
     const float* pg = p + g * CS;
-    float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+    unsigned long long xlo = 0ull, xhi = 0ull;      // (+0, +0) pairs
     if (g == 0) {
       const float4 sv = lds4(p + n * CS);
-      x = make_float4(a * sv.x, a * sv.y, a * sv.z, a * sv.w);
+      xlo = pack2(a * sv.x, a * sv.y);
+      xhi = pack2(a * sv.z, a * sv.w);
     }
+    // per point the same fma(-c, v, x) sequence as proj_point: bit-identical
 #pragma unroll
     for (int k = 0; k < KN; ++k) {
       const float* pk = (k + 1 < KN || g + SQ_NG * k < n) ? pg + SQ_NG * k * CS : p + n * CS;
-      const float4 v = lds4(pk);
-      const float cc = coef[SQ_NG * k];
-      x.x = fmaf(-cc, v.x, x.x);
-      x.y = fmaf(-cc, v.y, x.y);
-      x.z = fmaf(-cc, v.z, x.z);
-      x.w = fmaf(-cc, v.w, x.w);
+      const ulonglong2 v = lds2x2(pk);
+      const unsigned long long cc = coef[SQ_NG * k];
+      xlo = ffma2(cc, v.x, xlo);
+      xhi = ffma2(cc, v.y, xhi);
     }
-    return x;
+    const float2 lo = unpack2(xlo), hi = unpack2(xhi);
+    return make_float4(lo.x, lo.y, hi.x, hi.y);
   }
   template <int KN, int CS>
   __device__ __forceinline__ float proj_point(const float* p, int sslot, float a) const {
@@ -407,17 +437,15 @@ struct StreamEngine {
   __device__ __forceinline__ void dots_quad(const float* p, const float4& x4, const float4& w4,
                                             StreamAcc<SQ_KC>& A) const {
     const float* pg = p + g * CS;
+    const unsigned long long xlo = pack2(x4.x, x4.y), xhi = pack2(x4.z, x4.w);
+    const unsigned long long wlo = pack2(w4.x, w4.y), whi = pack2(w4.z, w4.w);
 #pragma unroll
     for (int k = 0; k < KN; ++k) {
       const float* pk = (k + 1 < KN || g + SQ_NG * k < n) ? pg + SQ_NG * k * CS : p + n * CS;
-      const float4 v = lds4(pk);
-      float px = v.x * x4.x, pw = v.x * w4.x;
-      px = fmaf(v.y, x4.y, px);
-      pw = fmaf(v.y, w4.y, pw);
-      px = fmaf(v.z, x4.z, px);
-      pw = fmaf(v.z, w4.z, pw);
-      px = fmaf(v.w, x4.w, px);
-      pw = fmaf(v.w, w4.w, pw);
+      const ulonglong2 v = lds2x2(pk);
+      const float2 tx = unpack2(ffma2(v.y, xhi, fmul2(v.x, xlo)));   // (v0 x0 + v2 x2, v1 x1 + v3 x3)
+      const float2 tw = unpack2(ffma2(v.y, whi, fmul2(v.x, wlo)));
+      const float px = tx.x + tx.y, pw = tw.x + tw.y;
       E::kahan(A.xs[k], A.xc[k], px);
       E::kahan(A.ws[k], A.wc[k], pw);
     }
@@ -615,6 +643,10 @@ struct StreamEngine {
     depth = nst - 1 - lag;                // the host guarantees depth >= 1
     // column slots n..4kn-1 of the last group get a zero coefficient
     if (e.tid >= n && e.tid < SQ_NG * kn) e.S.coefc[e.tid] = 0.f;
+    if (e.tid < SQ_NG * kn) {
+      const float c = (e.tid < n) ? -e.S.coefc[e.tid] : 0.f;
+      const_cast<unsigned long long*>(coef2)[e.tid] = pack2(c, c);
+    }
     // generic writes to the stage area (partials scratch, the last CTA's small
     // matrices) are ordered before this pass's TMA writes into it
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -704,7 +736,8 @@ __global__ void __launch_bounds__(NT, 1)
   }
   __syncthreads();
   StreamEngine<Op> t(e, maps, sp, reinterpret_cast<float*>(smem_raw + LY::ring_off()), stages, bar0,
-                     &S.stop, reinterpret_cast<int4*>(smem_raw + LY::tab_off()));
+                     &S.stop, reinterpret_cast<int4*>(smem_raw + LY::tab_off()),
+                     reinterpret_cast<const unsigned long long*>(smem_raw + LY::c2_off()));
   t.run_hybrid();
 }
 
