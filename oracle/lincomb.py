@@ -76,3 +76,53 @@ def lincomb_krylov(matvec, bs, tau: float, m: int, nsub: int = 1, variant: str =
         u = y[0][:N].copy()
         infos.append(info)
     return u, infos
+
+
+def step_factor(err: float, tol_abs: float, m: int) -> float:
+    """Sub-step size factor of the adaptive control (this build's controller; the
+    paper takes KIOPS's, which it does not reproduce): 0.9 (tol/err)^(1/(m+1)),
+    clamped to [0.2, 4]; 4 when the estimate is zero (exact projection)."""
+    if err <= 0.0:
+        return 4.0
+    return min(4.0, max(0.2, 0.9 * (tol_abs / err) ** (1.0 / (m + 1))))
+
+
+def lincomb_adaptive(matvec, bs, tau: float, m: int, tol: float, nsub0: int = 1,
+                     variant: str = "mgs", max_substeps: int = 100000):
+    """u = sum_j tau^j phi_j(tau A) b_j in sub-steps chosen by the a-posteriori
+    estimate err = beta dt H_{m+1,m} |e_m^T phi_1(dt H_m) e_1| of each projection:
+    a sub-step is accepted when err <= tol * beta (beta the norm of its augmented
+    start vector) and the next size is dt * step_factor; a rejected one is
+    retried with dt * min(0.9, step_factor).  A sub-step shorter than
+    tau * 2^-30 is accepted regardless (reported as not converged).  Starts with
+    dt = tau / nsub0.  Returns (u, info) with the accepted sizes, the number of
+    rejections and whether every accepted step met the tolerance."""
+    bs = [np.asarray(b, dtype=np.float64) for b in bs]
+    p = len(bs) - 1
+    N = bs[0].size
+    mv = aug_matvec(matvec, bs)
+    u = bs[0].copy()
+    t, dt = 0.0, tau / nsub0
+    sizes, rejected, converged = [], 0, True
+    floor = abs(tau) * 2.0 ** -30
+    while len(sizes) + rejected < max_substeps:
+        last = abs(dt) >= abs(tau - t)
+        if last:
+            dt = tau - t
+        w0 = np.concatenate([u, aug_tail(p, t)])
+        y, info = phiv(mv, w0, dt, 0, m, variant)
+        err = 0.0 if info["breakdown"] else float(info["err_est"])
+        tol_abs = tol * float(info["beta"])
+        if err <= tol_abs or abs(dt) <= floor:
+            if err > tol_abs:
+                converged = False
+            u = y[0][:N].copy()
+            sizes.append(dt)
+            if last:
+                return u, dict(sizes=sizes, rejected=rejected, converged=converged)
+            t += dt
+            dt *= step_factor(err, tol_abs, m)
+        else:
+            rejected += 1
+            dt *= min(0.9, step_factor(err, tol_abs, m))
+    return u, dict(sizes=sizes, rejected=rejected, converged=False)

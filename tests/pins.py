@@ -541,3 +541,19 @@ def integrator_orders(T=1.0, steps=(8, 16, 32)):
     _ORDER_CACHE.clear()
     _ORDER_CACHE[key] = out
     return out
+
+
+def pin_lincomb_adaptive(tol=1e-10, tau=2.0, m=12):
+    """Adaptive sub-steps on a stiff non-symmetric operator where one m-step
+    projection is far from the tolerance: the result is within a small multiple
+    of tol of the dense augmented exponential, it took more than one sub-step,
+    and every accepted sub-step met the tolerance.  Returns (error relative to
+    tol, number of sub-steps, converged)."""
+    cfg = W.advdiff2d(12, diff=0.05, vel=(1.0, 0.5))
+    A = OP.from_workload(cfg, {}).toarray()
+    rng = np.random.default_rng(25)
+    bs = [rng.uniform(-1, 1, A.shape[0]) for _ in range(3)]
+    ref = OE.phi_combination_dense(A, bs, tau, expm=scipy.linalg.expm)
+    u, info = OL.lincomb_adaptive(lambda x: A @ x, bs, tau, m, tol)
+    err = float(np.linalg.norm(u - ref) / np.linalg.norm(ref))
+    return err / tol, len(info["sizes"]), info["converged"]

@@ -19,3 +19,9 @@ def test_lincomb_substeps_match_dense_augmented_exponential():
 
 def test_lincomb_single_vector_is_a_phi_product():
     assert pins.pin_lincomb_single_vector() < 1e-11
+
+
+def test_lincomb_adaptive_substeps_meet_the_tolerance():
+    err_over_tol, nsteps, converged = pins.pin_lincomb_adaptive()
+    assert converged and nsteps > 1
+    assert err_over_tol < 10.0

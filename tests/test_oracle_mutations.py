@@ -167,3 +167,12 @@ def test_srerk3_weight_slip_is_caught(monkeypatch):
         assert pins.integrator_orders()["srerk3"] < 2.5
     finally:
         pins._ORDER_CACHE.clear()
+
+
+def test_lincomb_stale_tail_is_caught(monkeypatch):
+    # sub-steps restarting the extra entries from e_p instead of exp(tK) e_p
+    from oracle import lincomb as OL
+    orig = OL.aug_tail
+    monkeypatch.setattr(OL, "aug_tail", lambda p, t: orig(p, 0.0))
+    assert pins.pin_lincomb_substeps_vs_dense() > 1e-3
+    assert pins.pin_lincomb_adaptive()[0] > 1e3
