@@ -201,6 +201,32 @@ lsa_status lsa_phiv_lincomb(const lsa_op* op, const double* b, int p, double tau
                             double tol, int variant, int precision, double* u, void* work,
                             size_t work_bytes, lsa_stats* stats, void* stream);
 
+/* lsa_phiv_lincomb with sub-steps chosen by the a-posteriori estimate of each
+ * projection (this library's controller; the paper uses KIOPS's, which it
+ * cites but does not give).  A sub-step of size dt from state (t, u_t) is one
+ * m-step projection of the augmented operator; with err = beta dt H_{m+1,m}
+ * |e_m^T phi_1(dt H_m) e_1| and beta the norm of its augmented start vector it
+ * is accepted when err <= tol * beta, and the next size is dt * f,
+ * f = 0.9 (tol beta / err)^(1/(m+1)) clamped to [0.2, 4] (4 after an exact
+ * projection); a rejected sub-step is retried with dt * min(f, 0.9).  The first
+ * size is tau / nsub0; a sub-step shorter than |tau| 2^-30 is accepted
+ * regardless.
+ *  tol        > 0, relative to beta.      max_substeps  accepted + rejected cap.
+ *  u          dev, N doubles: the result; may be b_0 itself.
+ *  scratch    dev, N doubles, distinct from u and from b (the trial sub-step
+ *             result while u holds the accepted state, or the reverse).
+ *  substeps, rejected  (host, may be NULL): accepted and rejected sub-steps.
+ *  Other arguments as lsa_phiv_lincomb.  The stream is synchronised after
+ *  every sub-step (the controller reads the estimate on the host).
+ * Returns LSA_NOT_CONVERGED when a sub-step at the size floor missed the
+ * tolerance or max_substeps ended the process before tau (u then holds the
+ * last accepted state), LSA_BREAKDOWN after an exact projection, else LSA_OK,
+ * or the first error. */
+lsa_status lsa_phiv_lincomb_adaptive(const lsa_op* op, const double* b, int p, double tau, double tol,
+                                     int m, int nsub0, int max_substeps, int variant, int precision,
+                                     double* u, double* scratch, void* work, size_t work_bytes,
+                                     lsa_stats* stats, int* substeps, int* rejected, void* stream);
+
 /* Exponential-integrator building blocks (Sect. 4) besides the phi products.
  * lsa_rhs: f = F(u) for the Gray-Scott system whose Jacobian at a state is
  *   the LSA_OP_GRAYSCOTT2D operator: F(u, v) = [Du Lap u - u v^2 + F (1 - u);

@@ -101,6 +101,7 @@ def lincomb_adaptive(matvec, bs, tau: float, m: int, tol: float, nsub0: int = 1,
     p = len(bs) - 1
     N = bs[0].size
     mv = aug_matvec(matvec, bs)
+    m = min(m, N + p)
     u = bs[0].copy()
     t, dt = 0.0, tau / nsub0
     sizes, rejected, converged = [], 0, True
@@ -111,7 +112,7 @@ def lincomb_adaptive(matvec, bs, tau: float, m: int, tol: float, nsub0: int = 1,
             dt = tau - t
         w0 = np.concatenate([u, aug_tail(p, t)])
         y, info = phiv(mv, w0, dt, 0, m, variant)
-        err = 0.0 if info["breakdown"] else float(info["err_est"])
+        err = 0.0 if info["breakdown"] else abs(float(info["err_est"]))
         tol_abs = tol * float(info["beta"])
         if err <= tol_abs or abs(dt) <= floor:
             if err > tol_abs:

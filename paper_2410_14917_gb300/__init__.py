@@ -19,7 +19,7 @@ import torch
 from . import _binding as B
 from ._binding import LsaError, LsaOp, LsaStats, PRECISIONS, VARIANTS, KINDS
 
-__all__ = ["Operator", "phiv", "phiv_lincomb", "phiv_noalloc", "arnoldi", "matvec", "expm_phi", "workspace_bytes", "read_stats",
+__all__ = ["Operator", "phiv", "phiv_lincomb", "phiv_lincomb_adaptive", "phiv_noalloc", "arnoldi", "matvec", "expm_phi", "workspace_bytes", "read_stats",
            "selftest_barrier_timeout", "max_m", "LsaError", "Workspace", "Batch", "phiv_batched",
            "phiv_vjp", "Phi1GrayScott"]
 
@@ -191,6 +191,31 @@ def phiv_lincomb(op: Operator, b: torch.Tensor, tau: float, m: int, nsub: int = 
                                   ctypes.byref(s) if stats else None, _stream_ptr(stream))
     _check(st, "lsa_phiv_lincomb")
     return u, (s.as_dict() if stats else None)
+
+
+def phiv_lincomb_adaptive(op: Operator, b: torch.Tensor, tau: float, m: int, tol: float, nsub0: int = 1,
+                          max_substeps: int = 10000, variant="hcwy", u=None, work=None, stream=None):
+    """phiv_lincomb with sub-steps chosen by the a-posteriori estimate of each
+    projection (lsa_phiv_lincomb_adaptive); returns (u, stats dict with the
+    accepted and rejected sub-step counts)."""
+    if b.dtype != torch.float64 or not b.is_cuda or not b.is_contiguous() or b.dim() != 2:
+        raise ValueError("b must be a contiguous (p+1, N) float64 CUDA tensor")
+    p = b.shape[0] - 1
+    N = b.shape[1]
+    u = torch.empty(N, dtype=torch.float64, device=b.device) if u is None else u
+    scratch = torch.empty(N, dtype=torch.float64, device=b.device)
+    work = work or Workspace.for_call(op, min(m, N + p), 0, "fp64")
+    s = LsaStats()
+    nacc, nrej = ctypes.c_int(0), ctypes.c_int(0)
+    st = B.lib().lsa_phiv_lincomb_adaptive(ctypes.byref(op.c), _ptr(b), int(p), float(tau), float(tol),
+                                           int(m), int(nsub0), int(max_substeps), VARIANTS[variant],
+                                           PRECISIONS["fp64"], _ptr(u), _ptr(scratch),
+                                           ctypes.c_void_p(work.ptr), work.nbytes, ctypes.byref(s),
+                                           ctypes.byref(nacc), ctypes.byref(nrej), _stream_ptr(stream))
+    _check(st, "lsa_phiv_lincomb_adaptive")
+    d = s.as_dict()
+    d.update(substeps=nacc.value, rejected=nrej.value)
+    return u, d
 
 
 def phiv_noalloc(op: Operator, v: torch.Tensor, h: float, p: int, m: int, tol: float = 0.0,

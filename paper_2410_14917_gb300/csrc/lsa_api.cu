@@ -555,6 +555,125 @@ lsa_status lsa_phiv_lincomb(const lsa_op* op, const double* b, int p, double tau
   return worst;
 }
 
+// Step-size factor of the adaptive sub-steps: 0.9 (tol/err)^(1/(m+1)) clamped
+// to [0.2, 4]; 4 when the projection was exact (this library's controller).
+static double lincomb_step_factor(double err, double tol_abs, int m) {
+  if (!(err > 0.0)) return 4.0;
+  const double f = 0.9 * pow(tol_abs / err, 1.0 / (m + 1));
+  return f < 0.2 ? 0.2 : (f > 4.0 ? 4.0 : f);
+}
+
+lsa_status lsa_phiv_lincomb_adaptive(const lsa_op* op, const double* b, int p, double tau, double tol,
+                                     int m, int nsub0, int max_substeps, int variant, int precision,
+                                     double* u, double* scratch, void* work, size_t work_bytes,
+                                     lsa_stats* stats, int* substeps, int* rejected, void* stream) {
+  if (!b || !u || !scratch || u == scratch) return LSA_ERR_ARG;
+  if (variant < LSA_MGS || variant > LSA_IOCGS || precision != LSA_FP64) return LSA_ERR_ARG;
+  if (p < 0 || p > PMAX || !isfinite(tau) || !(tol > 0.0) || !isfinite(tol) || nsub0 < 1 ||
+      max_substeps < 1)
+    return LSA_ERR_ARG;
+  if (!op || op->kind > LSA_OP_ADR3D) return LSA_ERR_ARG;
+  long long N = lsa_op_dof(op);
+  if (N < 1 || m < 1) return LSA_ERR_ARG;
+  if (m > N + p) m = (int)(N + p);
+  Prepared pr;
+  lsa_status st = prepare(op, m, precision, work, work_bytes, &pr);
+  if (st != LSA_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  lsa_stats acc;
+  memset(&acc, 0, sizeof(acc));
+  acc.m_eff = m;
+  const double* cur = b;                       // the accepted state (b_0 at t = 0)
+  double t = 0.0, dt = tau / nsub0;
+  const double floor_dt = fabs(tau) * ldexp(1.0, -30);
+  int nacc = 0, nrej = 0;
+  bool done = false, converged = true;
+  lsa_status worst = LSA_OK;
+  while (nacc + nrej < max_substeps) {
+    const bool last = fabs(dt) >= fabs(tau - t);
+    if (last) dt = tau - t;
+    double* out = (u != cur) ? u : scratch;    // never the accepted state
+    ArnoldiParams P = pr.P;
+    P.vin = cur;
+    P.variant = variant;
+    P.write_vlast = 0;
+    P.naug = p;
+    P.baug = b;
+    P.aug_t = t;
+    CallTimer tm(stats != nullptr, s);
+    cudaError_t e = launch_init(P.ctl, pr.d, nullptr, nullptr, precision, P.H, (m + 1) * m, P.vin, P.V, s);
+    tm.mark(0);
+    if (e == cudaSuccess) e = launch_arnoldi(P, precision, pr.L.G, s);
+    tm.mark(1);
+    SmallParams S;
+    memset(&S, 0, sizeof(S));
+    S.H = P.H;
+    S.ldh = m + 1;
+    S.ctl_in = P.ctl;
+    S.ctl = P.ctl;
+    S.m = m;
+    S.p = 0;
+    S.h = dt;
+    S.mats = (double*)(pr.w + pr.L.small);
+    S.C = (double*)(pr.w + pr.L.coefs);
+    S.ldc = MMAX + 2;
+    S.scale_out = 1;
+    S.timeout_ns = kTimeoutNs;
+    S.tol = 0.0;
+    if (e == cudaSuccess) e = launch_expm(S, s);
+    tm.mark(2);
+    if (e == cudaSuccess) e = launch_combine(P.V, precision, N, S.C, S.ldc, 0, P.ctl, out, s);
+    tm.mark(3);
+    if (e != cudaSuccess) return LSA_ERR_CUDA;
+    lsa_stats one;
+    lsa_status r = fill_stats(P.ctl, &one, s);  // the controller needs the estimate on the host
+    if (r < 0) {
+      if (stats) { acc.status = r; *stats = acc; }
+      return r;
+    }
+    acc.grid_syncs += one.grid_syncs;
+    acc.grid_barriers += one.grid_barriers;
+    acc.norm_fallbacks += one.norm_fallbacks;
+    acc.ms_arnoldi += tm.ms(0, 1);
+    acc.ms_expm += tm.ms(1, 2);
+    acc.ms_combine += tm.ms(2, 3);
+    acc.launches += 4;
+    const double err = one.breakdown ? 0.0 : one.err_est;
+    const double tol_abs = tol * one.beta;
+    if (err <= tol_abs || fabs(dt) <= floor_dt) {
+      if (err > tol_abs) converged = false;
+      cur = out;
+      ++nacc;
+      if (one.m_eff < acc.m_eff) acc.m_eff = one.m_eff;
+      acc.breakdown |= one.breakdown;
+      if (nacc == 1) acc.beta = one.beta;
+      if (one.err_est > acc.err_est) acc.err_est = one.err_est;
+      acc.h_last = one.h_last;
+      if (r == LSA_BREAKDOWN && worst == LSA_OK) worst = LSA_BREAKDOWN;
+      if (last) { done = true; break; }
+      t += dt;
+      dt *= lincomb_step_factor(err, tol_abs, m);
+    } else {
+      ++nrej;
+      const double f = lincomb_step_factor(err, tol_abs, m);
+      dt *= f < 0.9 ? f : 0.9;
+    }
+  }
+  if (cur != u) {
+    if (cudaMemcpyAsync(u, cur, (size_t)N * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return LSA_ERR_CUDA;
+  }
+  if (!done || !converged) worst = LSA_NOT_CONVERGED;
+  if (substeps) *substeps = nacc;
+  if (rejected) *rejected = nrej;
+  if (stats) {
+    acc.status = worst;
+    acc.arnoldi_kernel = 0;
+    *stats = acc;
+  }
+  return worst;
+}
+
 lsa_status lsa_expm_phi(const double* H, int ldh, int m, double h, int p, double* C, void* work,
                         size_t work_bytes, void* stream) {
   if (!H || !C || m < 1 || m > MMAX || ldh < m || p < 0 || p > PMAX || !isfinite(h))

@@ -154,3 +154,42 @@ def test_lincomb_largest_p_and_m():
     ref, _ = OL.lincomb_krylov(lambda x: A @ x, list(b), tau, 64, 1, "mgs")
     u, st = lsa.phiv_lincomb(op, bd, tau, 64, 1, variant="hcwy")
     assert rel(u, ref) < FP64_TOL
+
+
+@pytest.mark.parametrize("variant", ["hcwy", "mgs"])
+def test_lincomb_adaptive_matches_oracle(variant):
+    p, tau, m, tol = 3, 2.0, 16, 1e-10
+    cfg = case("grayscott2d")
+    lsa, op, A, b, bd = setup(cfg, p)
+    ref, info = OL.lincomb_adaptive(lambda x: A @ x, list(b), tau, m, tol)
+    u, st = lsa.phiv_lincomb_adaptive(op, bd, tau, m, tol, variant=variant)
+    assert st["status"] == 0 and info["converged"]
+    assert abs(st["substeps"] - len(info["sizes"])) <= 1 and st["substeps"] > 1
+    assert rel(u, ref) < 20 * tol
+
+
+def test_lincomb_adaptive_against_dense_and_in_place():
+    p, tau, m, tol = 2, 1.5, 12, 1e-9
+    cfg = W.advdiff2d(16, m=m, diff=0.02)
+    lsa, op, A, b, bd = setup(cfg, p)
+    dense = OE.phi_combination_dense(A.toarray(), list(b), tau, expm=OE.scipy_expm)
+    u, st = lsa.phiv_lincomb_adaptive(op, bd, tau, m, tol, u=bd[0])
+    assert st["substeps"] > 1
+    assert rel(bd[0], dense) < 20 * tol
+
+
+def test_lincomb_adaptive_loose_tolerance_is_one_step():
+    cfg = case("advdiff2d")
+    lsa, op, A, b, bd = setup(cfg, 2)
+    u1, st = lsa.phiv_lincomb_adaptive(op, bd, 0.5, cfg["m"], 1.0)
+    u0, _ = lsa.phiv_lincomb(op, bd, 0.5, cfg["m"], 1, variant="hcwy")
+    assert st["substeps"] == 1 and st["rejected"] == 0
+    assert torch.equal(u0, u1)
+
+
+def test_lincomb_adaptive_reports_the_substep_cap():
+    p, tau, m, tol = 3, 2.0, 8, 1e-12
+    cfg = case("grayscott2d")
+    lsa, op, A, b, bd = setup(cfg, p)
+    u, st = lsa.phiv_lincomb_adaptive(op, bd, tau, m, tol, max_substeps=2)
+    assert st["status"] == 2          # LSA_NOT_CONVERGED: tau not reached within the cap
