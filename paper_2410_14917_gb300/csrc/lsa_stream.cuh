@@ -560,7 +560,8 @@ struct StreamEngine {
     STask Tp = task_of(cur);
     for (int i = 0; i < ntask; ++i) {
       const STask T = task_of(cur);
-      if (wait_full(s)) project(T, s, ps, i & (SQ_NRING - 1), A);
+      // a warp projects only if all its lanes saw the stage (warp shuffles inside)
+      if (__all_sync(0xffffffffu, wait_full(s))) project(T, s, ps, i & (SQ_NRING - 1), A);
       const bool refill = i + depth < ntask;
       const STask Ti = task_of(icur);
       if (refill && e.tid == 0) expect(Ti, si);
