@@ -45,7 +45,10 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) of one launch of the dominant kernel from an ncu
 # capture of the current kernel (profiles/k_arnoldi_grayscott2d_512_fp64.md);
 # a workload without an up-to-date capture reports null.
-PROFILED_TRAFFIC = {("grayscott2d_512", "fp64", "hcwy"): 9.516027e9 + 0.801385e9}
+# The 3D line's capture is of the 160^3 case, scaled by the unknowns (4.096x)
+# (profiles/k_arnoldi_stream_adr3d_160_fp32.md).
+PROFILED_TRAFFIC = {("grayscott2d_512", "fp64", "hcwy"): 9.516027e9 + 0.801385e9,
+                    ("adr3d_256", "fp32", "hcwy"): (16.750895e9 + 1.468495e9) * (256 / 160) ** 3}
 
 
 def parse():
@@ -920,8 +923,10 @@ def main():
     else:
         achieved = byts / (ms_a / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": None,
-                "kernel": "k_arnoldi (persistent hybrid Arnoldi)", "peak_source": f"{peak_kind} hbm_gbs",
+                "frac": achieved / hbm_peak,
+                "traffic": PROFILED_TRAFFIC.get((cfg["name"], args.precision, args.variant)),
+                "kernel": "k_arnoldi_stream (persistent hybrid Arnoldi, streaming float32 form)",
+                "peak_source": f"{peak_kind} hbm_gbs",
                 "algorithmic_bytes": byts, "algorithmic_flops": flops}
 
     line = {"metric": METRIC, "value": value, "unit": "phiv/s", "n_gpus": world,
