@@ -925,7 +925,8 @@ def main():
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak,
                 "traffic": PROFILED_TRAFFIC.get((cfg["name"], args.precision, args.variant)),
-                "kernel": "k_arnoldi_stream (persistent hybrid Arnoldi, streaming float32 form)",
+                "kernel": {0: "k_arnoldi", 1: "k_arnoldi_tma", 2: "k_arnoldi_stream"}[st0["arnoldi_kernel"]]
+                          + " (persistent Arnoldi, float32 basis)",
                 "peak_source": f"{peak_kind} hbm_gbs",
                 "algorithmic_bytes": byts, "algorithmic_flops": flops}
 
