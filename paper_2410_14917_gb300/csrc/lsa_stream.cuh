@@ -393,14 +393,15 @@ struct StreamEngine {
     }
   }
 
-  // x (quad) = a*src - sum_c coef_c V_c over this thread's KN column slots;
-  // `p` points at slot 0 of the quad, `cs` is the slot stride.
-  // x (quad) = a*src - sum_c coef_c V_c over this thread's KN column slots;
-  // `p` points at slot 0 of the quad, CS is the slot stride.  Slots below
-  // KN-1 are always columns (4(KN-1) + 3 < n + 3); the last one may be past n
-  // and then reads the source slot with a zero coefficient.
-  template <int KN, int CS>
-  __device__ __forceinline__ float4 proj_quad(const float* p, float a) const {
+  // x (quad) = a*src - sum_c coef_c V_c over this thread's column slots
+  // c = g, g+4, ... (p points at slot 0 of the quad, CS is the slot stride);
+  // slots below kn-1 are always columns (4(kn-1) + 3 < n + 3); the last one may
+  // be past n and then reads the source slot with a zero coefficient.
+  // The inner loops for the pass's column count: unrolled to the largest count
+  // with an exit after kn slots (one copy of each loop instead of one per count,
+  // so the task loop stays small in the instruction cache).
+  template <int CS>
+  __device__ __forceinline__ float4 proj_quad_n(const float* p, float a) const {
     const unsigned long long* coef = coef2 + g;
     const float* pg = p + g * CS;
     unsigned long long xlo = 0ull, xhi = 0ull;      // (+0, +0) pairs
@@ -409,10 +410,11 @@ struct StreamEngine {
       xlo = pack2(a * sv.x, a * sv.y);
       xhi = pack2(a * sv.z, a * sv.w);
     }
-    // per point the same fma(-c, v, x) sequence as proj_point: bit-identical
+    // per point the same fma(-c, v, x) sequence as proj_point_n: bit-identical
 #pragma unroll
-    for (int k = 0; k < KN; ++k) {
-      const float* pk = (k + 1 < KN || g + SQ_NG * k < n) ? pg + SQ_NG * k * CS : p + n * CS;
+    for (int k = 0; k < SQ_KC; ++k) {
+      if (k >= kn) break;
+      const float* pk = (k + 1 < kn || g + SQ_NG * k < n) ? pg + SQ_NG * k * CS : p + n * CS;
       const ulonglong2 v = lds2x2(pk);
       const unsigned long long cc = coef[SQ_NG * k];
       xlo = ffma2(cc, v.x, xlo);
@@ -421,67 +423,36 @@ struct StreamEngine {
     const float2 lo = unpack2(xlo), hi = unpack2(xhi);
     return make_float4(lo.x, lo.y, hi.x, hi.y);
   }
-  template <int KN, int CS>
-  __device__ __forceinline__ float proj_point(const float* p, int sslot, float a) const {
+  template <int CS>
+  __device__ __forceinline__ float proj_point_n(const float* p, int sslot, float a) const {
     const float* coef = e.S.coefc + g;
     const float* pg = p + g * CS;
     float x = (g == 0) ? a * p[sslot * CS] : 0.f;
 #pragma unroll
-    for (int k = 0; k < KN; ++k) {
-      const float* pk = (k + 1 < KN || g + SQ_NG * k < n) ? pg + SQ_NG * k * CS : p + sslot * CS;
+    for (int k = 0; k < SQ_KC; ++k) {
+      if (k >= kn) break;
+      const float* pk = (k + 1 < kn || g + SQ_NG * k < n) ? pg + SQ_NG * k * CS : p + sslot * CS;
       x = fmaf(-coef[SQ_NG * k], *pk, x);
     }
     return x;
   }
-  template <int KN, int CS>
-  __device__ __forceinline__ void dots_quad(const float* p, const float4& x4, const float4& w4,
-                                            StreamAcc<SQ_KC>& A) const {
+  template <int CS>
+  __device__ __forceinline__ void dots_quad_n(const float* p, const float4& x4, const float4& w4,
+                                              StreamAcc<SQ_KC>& A) const {
     const float* pg = p + g * CS;
     const unsigned long long xlo = pack2(x4.x, x4.y), xhi = pack2(x4.z, x4.w);
     const unsigned long long wlo = pack2(w4.x, w4.y), whi = pack2(w4.z, w4.w);
 #pragma unroll
-    for (int k = 0; k < KN; ++k) {
-      const float* pk = (k + 1 < KN || g + SQ_NG * k < n) ? pg + SQ_NG * k * CS : p + n * CS;
+    for (int k = 0; k < SQ_KC; ++k) {
+      if (k >= kn) break;
+      const float* pk = (k + 1 < kn || g + SQ_NG * k < n) ? pg + SQ_NG * k * CS : p + n * CS;
       const ulonglong2 v = lds2x2(pk);
       const float2 tx = unpack2(ffma2(v.y, xhi, fmul2(v.x, xlo)));   // (v0 x0 + v2 x2, v1 x1 + v3 x3)
       const float2 tw = unpack2(ffma2(v.y, whi, fmul2(v.x, wlo)));
-      const float px = tx.x + tx.y, pw = tw.x + tw.y;
-      E::kahan(A.xs[k], A.xc[k], px);
-      E::kahan(A.ws[k], A.wc[k], pw);
+      E::kahan(A.xs[k], A.xc[k], tx.x + tx.y);
+      E::kahan(A.ws[k], A.wc[k], tw.x + tw.y);
     }
   }
-
-  // Per-column-count (and stride) dispatch of the inner loops (kn = ceil(n/4)).
-#define LSA_SQ_CASES(X) X(0) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15)
-  template <int CS>
-  __device__ __forceinline__ float4 proj_quad_n(const float* p, float a) const {
-    switch (kn) {
-#define LSA_SQ_C(K) case K: return proj_quad<K, CS>(p, a);
-      LSA_SQ_CASES(LSA_SQ_C)
-#undef LSA_SQ_C
-      default: return proj_quad<16, CS>(p, a);
-    }
-  }
-  template <int CS>
-  __device__ __forceinline__ float proj_point_n(const float* p, int sslot, float a) const {
-    switch (kn) {
-#define LSA_SQ_C(K) case K: return proj_point<K, CS>(p, sslot, a);
-      LSA_SQ_CASES(LSA_SQ_C)
-#undef LSA_SQ_C
-      default: return proj_point<16, CS>(p, sslot, a);
-    }
-  }
-  template <int CS>
-  __device__ __forceinline__ void dots_quad_n(const float* p, const float4& x4, const float4& w4,
-                                              StreamAcc<SQ_KC>& A) const {
-    switch (kn) {
-#define LSA_SQ_C(K) case K: dots_quad<K, CS>(p, x4, w4, A); return;
-      LSA_SQ_CASES(LSA_SQ_C)
-#undef LSA_SQ_C
-      default: dots_quad<16, CS>(p, x4, w4, A); return;
-    }
-  }
-#undef LSA_SQ_CASES
 
   // Projection of task T from stage s into ring slot rs: x = a*src - sum_c coef_c V_c.
   __device__ __forceinline__ void project(const STask& T, int s, const SPass& ps, int rs, StreamAcc<SQ_KC>& A) {
