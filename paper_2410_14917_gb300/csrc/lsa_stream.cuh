@@ -156,25 +156,6 @@ struct StreamEngine {
     bool main;
   };
 
-  __device__ __forceinline__ STask task(int i) const {
-    const Tiling& tl = e.P.tl;
-    const int tl_i = i / tpt, k = i - tl_i * tpt;
-    const int t = blockIdx.x + tl_i * gridDim.x;
-    const int rr = t / tl.tiles_x;
-    STask T;
-    T.bx = t - rr * tl.tiles_x;
-    T.by = rr % tl.tiles_y;
-    const int bz = rr / tl.tiles_y;
-    if (DIM == 3) {
-      const int kk = stencil ? k - 1 : k;
-      T.z = bz * tl.ZS + kk;
-      T.main = kk >= 0 && kk < tl.ZS;
-    } else {
-      T.z = 0;
-      T.main = true;
-    }
-    return T;
-  }
   // Incremental walk over this CTA's tasks (divisions only when the tile changes).
   struct Cursor {
     int tl_i, k, bx, by, bz;
