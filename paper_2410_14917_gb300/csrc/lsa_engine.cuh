@@ -647,8 +647,19 @@ struct Engine {
       stage(P.T, np);
       for (int k = tid; k < np; k += NT) {
         double acc = -temp1[k];
-        if (P.variant != LSA_HNCWY)
-          for (int i = k + 1; i < np; ++i) acc = fma(-temp1[i], small[i * MMAX + k], acc);
+        if (P.variant != LSA_HNCWY) {
+          // four interleaved partial sums (fixed order: deterministic) shorten the chain
+          double a1 = 0.0, a2 = 0.0, a3 = 0.0, a4 = 0.0;
+          int i = k + 1;
+          for (; i + 3 < np; i += 4) {
+            a1 = fma(-temp1[i], small[i * MMAX + k], a1);
+            a2 = fma(-temp1[i + 1], small[(i + 1) * MMAX + k], a2);
+            a3 = fma(-temp1[i + 2], small[(i + 2) * MMAX + k], a3);
+            a4 = fma(-temp1[i + 3], small[(i + 3) * MMAX + k], a4);
+          }
+          for (; i < np; ++i) a1 = fma(-temp1[i], small[i * MMAX + k], a1);
+          acc += (a1 + a2) + (a3 + a4);
+        }
         small[np * MMAX + k] = acc;
         P.T[np * MMAX + k] = acc;
       }
@@ -723,10 +734,25 @@ struct Engine {
   }
 
   // small[r][k] = M[r][k] for r < rows, k < r (strictly lower part), from global.
+  // Eight loads per thread are issued before their stores, so their round trips
+  // to L2 overlap (the step runs in one CTA while the others wait).
   __device__ void stage(const double* M, int rows) {
-    for (int e = tid; e < rows * MMAX; e += NT) {
-      int r = e / MMAX, k = e - r * MMAX;
-      if (k < r) small[e] = __ldcg(M + e);
+    constexpr int U = 8;
+    const int total = rows * MMAX;
+    for (int e0 = tid; e0 < total; e0 += U * NT) {
+      double v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * NT;
+        const int r = e / MMAX, k = e - r * MMAX;
+        v[u] = (e < total && k < r) ? __ldcg(M + e) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * NT;
+        const int r = e / MMAX, k = e - r * MMAX;
+        if (e < total && k < r) small[e] = v[u];
+      }
     }
     __syncthreads();
   }
