@@ -477,10 +477,11 @@ def bench_batched(args, world, rank, local, bcfg):
 
 def adjoint_flops(cfg, m):
     """FP64 flops of one gradient evaluation: the forward phi product and the
-    product on A^T (N unknowns each) and four on the Frechet block operator
-    (2N unknowns each; its stencil is counted like the Gray-Scott one)."""
+    product on A^T (N unknowns each) and three on the Frechet block operator
+    (2N unknowns each; its stencil is counted like the Gray-Scott one; the F
+    derivative is a closed form)."""
     _, f = algorithmic_counts(cfg, "fp64", m)
-    return 2 * f + 4 * 2 * f
+    return 2 * f + 3 * 2 * f
 
 
 def bench_adjoint(args, world, rank, local, cfg):
@@ -498,20 +499,20 @@ def bench_adjoint(args, world, rank, local, cfg):
     d = {k: torch.from_numpy(v).to(dev) for k, v in inp.items()}
     op = lsa.Operator.from_workload(cfg, d)
     v, yt = d["v"], d["y_target"]
-    y = torch.empty((2, N), dtype=torch.float64, device=dev)
-    work = lsa.Workspace.for_call(op, m, 1, "fp64")
+    y = torch.empty((3, N), dtype=torch.float64, device=dev)
+    r = torch.empty(N, dtype=torch.float64, device=dev)
+    work = lsa.Workspace.for_call(op, m, 2, "fp64")
     vwork = lsa.Workspace(lsa.vjp_workspace_bytes(op, m), device=dev)
     stream = torch.cuda.current_stream()
     flush = None if args.no_flush else torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
-    def grad_eval(vv, tgt):
-        lsa.phiv(op, vv, h, 1, m, variant=args.variant, y=y, work=work, stats=False)
-        r = y[1] - tgt
-        return lsa.phiv_vjp(op, vv, h, m, r, y, variant=args.variant, work=vwork)
+    def grad_eval(vv, tgt, stats=False):
+        # forward with p = 2 (phi_2 feeds the closed-form F derivative), residual, gradient
+        lsa.phiv(op, vv, h, 2, m, variant=args.variant, y=y, work=work, stats=False)
+        lsa.axpby(1.0, y[1], -1.0, tgt, out=r)
+        return lsa.phiv_vjp(op, vv, h, m, r, y, variant=args.variant, work=vwork, stats=stats)
 
-    gv, gs, st = lsa.phiv_vjp(op, v, h, m, lsa.phiv(op, v, h, 1, m, variant=args.variant, y=y,
-                                                    work=work)[0][1] - yt, y, variant=args.variant,
-                              work=vwork, stats=True)
+    gv, gs, st = grad_eval(v, yt, stats=True)
     for _ in range(args.warmup):
         grad_eval(v, yt)
     torch.cuda.synchronize()
@@ -536,7 +537,7 @@ def bench_adjoint(args, world, rank, local, cfg):
         if flush is not None:
             flush.fill_(i & 0xFF)
         fwd[i][0].record(stream)
-        lsa.phiv(op, v, h, 1, m, variant=args.variant, y=y, work=work, stats=False)
+        lsa.phiv(op, v, h, 1, m, variant=args.variant, y=y[:2], work=work, stats=False)
         fwd[i][1].record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -571,7 +572,7 @@ def bench_adjoint(args, world, rank, local, cfg):
     achieved = flops / (ms_step / 1e3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-            "kernel": "whole gradient evaluation (six k_arnoldi launches with their small kernels)",
+            "kernel": "whole gradient evaluation (five k_arnoldi launches with their small kernels)",
             "peak_source": "FP64 FMA pipe from unit counts and max clock (152 SMs x 2 FMA/clk x 2.07 GHz)",
             "algorithmic_flops": flops}
     line = {"metric": METRIC, "value": value, "unit": "grad/s", "n_gpus": world,
@@ -582,14 +583,14 @@ def bench_adjoint(args, world, rank, local, cfg):
                        "precision": "fp64", "theta": ["Du", "Dv", "F", "k"],
                        "l2": "flushed between timed steps (256 MiB write)" if flush is not None
                        else "not flushed", "parallelism": f"replicas x{world}"},
-            "phiv_per_grad": 6,
+            "phiv_per_grad": 5,
             "vs_plain_fp64_forward": {"forward_ms": fwd_ms, "gradient_ms": ms_step,
                                       "ratio": ms_step / fwd_ms},
             "grid_syncs": st["grid_syncs"],
             "roofline": roof,
             "e2e": {"value": e2e_value, "unit": "grad/s", "h2d_bytes_per_step": 2 * N * 8,
                     "d2h_bytes_per_step": (N + 5) * 8},
-            "gpu_launches": (6 * 4 + 10 + 0) * args.steps,
+            "gpu_launches": (5 * 4 + 10 + 1) * args.steps,
             "clocks": clocks}
     if rank == 0 and world == 1 and not args.no_cpu:
         from oracle import adjoint as OAD

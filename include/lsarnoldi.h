@@ -277,18 +277,22 @@ lsa_status lsa_phiv_noalloc(const lsa_op* op, const double* v, double h, int p, 
  *   dL/dh     = r . (phi_0(hA)v - phi_1(hA)v) / h    (d/dh [h phi_1(hA)] = e^{hA})
  *   dL/dtheta = r . [phi_1(hK)[0; v]]_top, K = [[A, dA/dtheta], [0, A]]
  *               (LSA_OP_GRAYSCOTT2D_FRECHET: the block-triangular augmentation of
- *               the Frechet derivative of exp applied to Sect. 2.1's Eq. 7 matrix).
- * Six phi products with m Krylov steps each, all float64: one on A^T (N) and
- * four on K (2N); no Krylov basis is kept between calls (each is rebuilt).
+ *               the Frechet derivative of exp applied to Sect. 2.1's Eq. 7 matrix)
+ *               for theta = diff, diff2, k;
+ *   dL/dF     = -h r . (phi_1(hA)v - phi_2(hA)v)    (dA/dF = -I commutes with A;
+ *               phi_1' = phi_1 - phi_2 follows from Eq. 6).
+ * Four phi products with m Krylov steps each, all float64: one on A^T (N) and
+ * three on K (2N); no Krylov basis is kept between calls (each is rebuilt).
  *  op        LSA_OP_GRAYSCOTT2D descriptor of A(theta) (aux ignored).
- *  v, r      dev, N doubles.    y  dev, 2 x N doubles: phi_0(hA)v then phi_1(hA)v
- *            (lsa_phiv with p = 1 and the same h, m and variant).
+ *  v, r      dev, N doubles.    y  dev, 3 x N doubles: phi_0(hA)v, phi_1(hA)v,
+ *            phi_2(hA)v (lsa_phiv with p = 2 and the same h, m and variant; p
+ *            only enlarges the small exponential, not the Arnoldi process).
  *  h         finite and nonzero.   m, variant as lsa_phiv.
  *  grad_v    dev, N doubles (output).
  *  grad_s    dev, 5 doubles (output): dL/dh, dL/ddiff, dL/ddiff2, dL/dF, dL/dk.
  *  work      dev workspace of lsa_phiv_vjp_workspace_bytes(op, m), 256-byte aligned.
  * stats as lsa_phiv (when non-NULL: the calls synchronise, the worst status of
- * the six products is returned and their counters are summed). */
+ * the four products is returned and their counters are summed). */
 size_t lsa_phiv_vjp_workspace_bytes(const lsa_op* op, int m);
 lsa_status lsa_phiv_vjp(const lsa_op* op, const double* v, double h, int m, int variant,
                         const double* r, const double* y, double* grad_v, double* grad_s,

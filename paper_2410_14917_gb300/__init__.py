@@ -19,7 +19,7 @@ import torch
 from . import _binding as B
 from ._binding import LsaError, LsaOp, LsaStats, PRECISIONS, VARIANTS, KINDS
 
-__all__ = ["Operator", "phiv", "phiv_lincomb", "phiv_lincomb_adaptive", "phiv_noalloc", "arnoldi", "matvec", "expm_phi", "workspace_bytes", "read_stats",
+__all__ = ["Operator", "phiv", "phiv_lincomb", "phiv_lincomb_adaptive", "axpby", "phiv_noalloc", "arnoldi", "matvec", "expm_phi", "workspace_bytes", "read_stats",
            "selftest_barrier_timeout", "max_m", "LsaError", "Workspace", "Batch", "phiv_batched",
            "phiv_vjp", "Phi1GrayScott"]
 
@@ -218,6 +218,19 @@ def phiv_lincomb_adaptive(op: Operator, b: torch.Tensor, tau: float, m: int, tol
     return u, d
 
 
+def axpby(a: float, x: torch.Tensor, b: float, y: torch.Tensor, out=None, stream=None):
+    """out = a x + b y over float64 CUDA tensors of one size (lsa_axpby)."""
+    for t_, name in ((x, "x"), (y, "y")):
+        if t_.dtype != torch.float64 or not t_.is_cuda or not t_.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous float64 CUDA tensor")
+    if x.numel() != y.numel():
+        raise ValueError("x and y must have the same size")
+    out = torch.empty_like(x) if out is None else out
+    _check(B.lib().lsa_axpby(x.numel(), float(a), _ptr(x), float(b), _ptr(y), _ptr(out),
+                             _stream_ptr(stream)), "lsa_axpby", ok=(B.LSA_OK,))
+    return out
+
+
 def phiv_noalloc(op: Operator, v: torch.Tensor, h: float, p: int, m: int, tol: float = 0.0,
                  variant="hcwy", precision="fp64", y=None, stream=None, stats=True):
     """phiv through lsa_phiv_noalloc: the library's fixed static device workspace
@@ -400,14 +413,14 @@ def phiv_vjp(op: Operator, v: torch.Tensor, h: float, m: int, r: torch.Tensor, y
              variant="hcwy", work=None, stream=None, stats=False):
     """Vector-Jacobian product of y1 = phi_1(h A(theta)) v (Gray-Scott, float64)
     for the cotangent r: returns (dL/dv, tensor of dL/dh, dL/dDu, dL/dDv, dL/dF,
-    dL/dk on the device, stats or None).  y is the (2, N) output of
-    phiv(op, v, h, p=1, m) -- phi_0 and phi_1 products."""
+    dL/dk on the device, stats or None).  y is the (3, N) output of
+    phiv(op, v, h, p=2, m) -- the phi_0, phi_1 and phi_2 products."""
     N = v.numel()
     for t, name in ((v, "v"), (r, "r"), (y, "y")):
         if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
             raise ValueError(f"{name} must be a contiguous float64 CUDA tensor")
-    if r.numel() != N or y.numel() != 2 * N:
-        raise ValueError("r must have N elements and y 2N")
+    if r.numel() != N or y.numel() != 3 * N:
+        raise ValueError("r must have N elements and y 3N (phiv with p = 2)")
     grad_v = torch.empty_like(v)
     grad_s = torch.empty(5, dtype=torch.float64, device=v.device)
     work = work or Workspace(vjp_workspace_bytes(op, m), device=v.device)
@@ -422,8 +435,8 @@ def phiv_vjp(op: Operator, v: torch.Tensor, h: float, m: int, r: torch.Tensor, y
 class Phi1GrayScott(torch.autograd.Function):
     """y = phi_1(h A(theta)) v for the Gray-Scott Jacobian A(theta), theta =
     (Du, Dv, F, k), differentiable in v (CUDA float64), h and theta (CPU
-    float64 tensors).  The forward keeps v, h, theta and the phi_0 / phi_1
-    products; the backward recomputes every Krylov basis it needs through
+    float64 tensors).  The forward keeps v, h, theta and the phi_0 / phi_1 /
+    phi_2 products; the backward recomputes every Krylov basis it needs through
     lsa_phiv_vjp (no basis is stored).
 
         y = Phi1GrayScott.apply(v, h, theta, op, m, variant)
@@ -436,7 +449,7 @@ class Phi1GrayScott(torch.autograd.Function):
         hh = float(h)
         Du, Dv, F, k = (float(t) for t in theta)
         opt = op.derived(kind="grayscott2d", diff=Du, diff2=Dv, F=F, k=k)
-        y, _ = phiv(opt, v.contiguous(), hh, 1, m, variant=variant, stats=False)
+        y, _ = phiv(opt, v.contiguous(), hh, 2, m, variant=variant, stats=False)
         ctx.save_for_backward(v, y)
         ctx.opt, ctx.h, ctx.m, ctx.variant = opt, hh, m, variant
         ctx.theta_dev = theta.device

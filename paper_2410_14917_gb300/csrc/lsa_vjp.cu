@@ -6,7 +6,10 @@
 //   dL/dh     = r . (phi_0(hA)v - phi_1(hA)v) / h   (d/dh [h phi_1(hA)] = e^{hA}, Eq. 6)
 //   dL/dtheta = r . [phi_1(hK)[0; v]]_top,  K = [[A, dA/dtheta], [0, A]]
 //               (LSA_OP_GRAYSCOTT2D_FRECHET: Sect. 2.1's Eq. 7 with the
-//               block-triangular augmentation of the Frechet derivative of exp).
+//               block-triangular augmentation of the Frechet derivative of exp)
+//               for Du, Dv and k;
+//   dL/dF     = -h r . (phi_1(hA)v - phi_2(hA)v)   (dA/dF = -I commutes with A,
+//               and phi_1' = phi_1 - phi_2 by Eq. 6): no product of its own.
 // No basis is stored between the forward product and these calls: each call
 // rebuilds its Krylov basis from v, r and the operator (recomputation instead
 // of keeping V_m).
@@ -151,13 +154,17 @@ lsa_status lsa_phiv_vjp(const lsa_op* op, const double* v, double h, int m, int 
     return LSA_ERR_CUDA;
   // dL/dh = r . (phi_0 v - phi_1 v) / h
   if (launch_dot(r, y, y + N, N, 1.0 / h, part, grad_s, s) != cudaSuccess) return LSA_ERR_CUDA;
-  // dL/dtheta_k = r . top half of phi_1(h K_k) [0; v]
+  // dL/dF = -h r . (phi_1 v - phi_2 v): dA/dF = -I commutes with A, so the
+  // derivative is -h phi_1'(hA) v, and phi_1'(z) = phi_1(z) - phi_2(z) (Eq. 6)
+  if (launch_dot(r, y + N, y + 2 * N, N, -h, part, grad_s + 3, s) != cudaSuccess) return LSA_ERR_CUDA;
+  // dL/dtheta_k = r . top half of phi_1(h K_k) [0; v] for Du, Dv and k
   if (cudaMemsetAsync(z0, 0, (size_t)N * sizeof(double), s) != cudaSuccess ||
       cudaMemcpyAsync(z0 + N, v, (size_t)N * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
     return LSA_ERR_CUDA;
   lsa_op opK = *op;
   opK.kind = LSA_OP_GRAYSCOTT2D_FRECHET;
   for (int k = 0; k < 4; ++k) {
+    if (k == 2) continue;   // F: closed form above
     opK.aux = k;
     st = phi(&opK, z0);
     if (st < 0) return st;
@@ -165,7 +172,7 @@ lsa_status lsa_phiv_vjp(const lsa_op* op, const double* v, double h, int m, int 
   }
   if (stats) {
     if (cudaStreamSynchronize(s) != cudaSuccess) return LSA_ERR_CUDA;
-    acc.launches += 10 + 3;   // five dot products (two kernels each) and three copies
+    acc.launches += 10;       // five dot products (two kernels each)
     *stats = acc;
     return (lsa_status)acc.status;
   }

@@ -69,7 +69,7 @@ def test_vjp_matches_oracle_gradient(variant):
     h, m = cfg["h"], cfg["m"]
     A, dA = OAD.grayscott_parts(cfg, inp)
     ref = OAD.grads_krylov(A, dA, inp["v"], inp["y_target"], h, m)
-    y, _ = lsa.phiv(op, dev["v"], h, 1, m, variant=variant)
+    y, _ = lsa.phiv(op, dev["v"], h, 2, m, variant=variant)
     r = y[1] - dev["y_target"]
     gv, gs, st = lsa.phiv_vjp(op, dev["v"], h, m, r, y, variant=variant, stats=True)
     gs = gs.cpu().numpy()
@@ -128,7 +128,7 @@ def test_vjp_rejects_bad_arguments():
 
     cfg = small_case(16, m=10)
     lsa, inp, dev, op = setup(cfg)
-    y, _ = lsa.phiv(op, dev["v"], cfg["h"], 1, 10)
+    y, _ = lsa.phiv(op, dev["v"], cfg["h"], 2, 10)
     with pytest.raises(LsaError):
         lsa.phiv_vjp(op, dev["v"], 0.0, 10, dev["v"], y)                   # h = 0
     with pytest.raises(LsaError):
@@ -144,7 +144,7 @@ def test_adjoint_workload_full_size_matches_oracle():
     cfg = W.config(4)
     lsa, inp, dev, op = setup(cfg)
     h, m = cfg["h"], cfg["m"]
-    y, _ = lsa.phiv(op, dev["v"], h, 1, m, variant="hcwy")
+    y, _ = lsa.phiv(op, dev["v"], h, 2, m, variant="hcwy")
     r = y[1] - dev["y_target"]
     gv, gs, _ = lsa.phiv_vjp(op, dev["v"], h, m, r, y, variant="hcwy")
     A, dA = OAD.grayscott_parts(cfg, inp)
