@@ -133,15 +133,29 @@ struct StreamEngine {
   // per pass
   int n = 0, kn = 0, nst = 2, depth = 1, lag = 0, tpt = 1, ntask = 0, sbytes = 0;
   bool stencil = false;
+  float* vx = nullptr;      // columns the pass writes (x, w) and their edge records
+  float* vw = nullptr;
+  float* ex = nullptr;
+  float* ew = nullptr;
 
   // thread roles: quad q (4 consecutive x points of a row), column group g
   const int q, g, ly, lx4;
+  // this thread's point (lx4 + g, ly): its x-halo copy, if it has one, goes to the
+  // record of the tile edx away (left for lx = 0, right for lx = TX-1) at eoff
+  const bool edge;
+  const int edx, eoff;
+  // geometry in 32-bit units (a column has fewer than 2^31 points): row pitch,
+  // plane size, tiles per row, edge-record plane size
+  const int gnx, gplane, gtx, geplane;
 
   __device__ StreamEngine(E& en, const StreamMaps& m, const StreamParams& p, float* rg,
                           unsigned char* st, unsigned b, int* stop, int4* tab,
                           const unsigned long long* c2)
       : e(en), maps(m), sp(p), ring(rg), stages(st), full0(b), s_stop(stop), itab(tab), coef2(c2),
-        q(en.warp * 8 + (en.lane & 7)), g(en.lane >> 3), ly(q >> 2), lx4((q & 3) * 4) {}
+        q(en.warp * 8 + (en.lane & 7)), g(en.lane >> 3), ly(q >> 2), lx4((q & 3) * 4),
+        edge(lx4 + g == 0 || lx4 + g == TX - 1), edx(lx4 + g == 0 ? -1 : 1),
+        eoff((lx4 + g == 0 ? TY : 0) + ly), gnx(en.P.op.nx), gplane(en.P.op.nx * en.P.op.ny),
+        gtx(en.P.tl.tiles_x), geplane(en.P.tl.tiles_x * en.P.tl.tiles_y * 2 * TY) {}
 
   __device__ __forceinline__ const float* stage(int s) const {
     return reinterpret_cast<const float*>(stages + (size_t)s * sbytes);
@@ -360,17 +374,15 @@ struct StreamEngine {
     return v;
   }
 
-  // store value x of point (lx, ly) of tile T in column col, with its edge copy
-  __device__ __forceinline__ void store_point(const STask& T, int zz, int lx, int col, float x) const {
-    const DevOp& d = e.P.op;
-    const Tiling& tl = e.P.tl;
-    const long long gp = (long long)(T.bx * TX + lx) + (long long)d.nx * ((T.by * TY + ly) + (long long)d.ny * zz);
-    reinterpret_cast<float*>(e.P.V)[(long long)col * d.N + gp] = x;
-    if (lx == 0 || lx == TX - 1) {
-      // left column: right halo of the tile to the left; right column: left halo of the next
-      const int nb = lx == 0 ? (T.bx == 0 ? tl.tiles_x - 1 : T.bx - 1) : (T.bx + 1 == tl.tiles_x ? 0 : T.bx + 1);
-      const int side = lx == 0 ? 1 : 0;
-      e.P.E[(long long)col * (d.N / 8) + edge_slot(tl.tiles_x, tl.tiles_y, nb, T.by, zz) + side * TY + ly] = x;
+  // store this thread's value x of tile T, plane zz into column vc, with its
+  // edge copy into ec (the column's edge records): the left column is the right
+  // halo of the tile to the left, the right column the left halo of the next
+  __device__ __forceinline__ void store_point(const STask& T, int zz, float* vc, float* ec, float x) const {
+    vc[T.bx * TX + lx4 + g + gnx * (T.by * TY + ly) + gplane * zz] = x;
+    if (edge) {
+      int nb = T.bx + edx;
+      nb = nb < 0 ? gtx - 1 : (nb == gtx ? 0 : nb);
+      ec[geplane * zz + (T.by * gtx + nb) * (2 * TY) + eoff] = x;   // edge_slot(nb, T.by, zz) + eoff
     }
   }
 
@@ -448,7 +460,7 @@ struct StreamEngine {
     rg[(ly + 1) * SQ_RP + 4 + lx4 + g] = xg;
     if (T.main) {
       const int zz = (DIM == 3) ? wrapi(T.z, d.nz) : 0;
-      if (ps.xout_col >= 0) store_point(T, zz, lx4 + g, ps.xout_col, xg);
+      if (ps.xout_col >= 0) store_point(T, zz, vx, ex, xg);
       if (!stencil && (ps.self & SELF_XX)) E::kahan(A.ss[0], A.sc[0], xg * xg);
     }
     if (has_halo(T)) {
@@ -480,7 +492,7 @@ struct StreamEngine {
     float out[1];
     Op::template apply_f<float, SQ_RP>(cf, xm, x0, xp, o, f0, 0.f, out);
     const float w = out[0];
-    store_point(Td, zc, lx, ps.wout_col, w);
+    store_point(Td, zc, vw, ew, w);
     const float xs = x0[o];
     if (ps.self & SELF_XX) E::kahan(A.ss[0], A.sc[0], xs * xs);
     if (ps.self & SELF_XW) E::kahan(A.ss[1], A.sc[1], xs * w);
@@ -586,6 +598,14 @@ struct StreamEngine {
     n = ps.ncp;
     kn = (n + SQ_NG - 1) / SQ_NG;
     stencil = ps.wout_col >= 0;
+    {
+      const long long N = e.P.op.N;
+      float* V = reinterpret_cast<float*>(e.P.V);
+      vx = ps.xout_col >= 0 ? V + (long long)ps.xout_col * N : nullptr;
+      ex = ps.xout_col >= 0 ? e.P.E + (long long)ps.xout_col * (N / 8) : nullptr;
+      vw = stencil ? V + (long long)ps.wout_col * N : nullptr;
+      ew = stencil ? e.P.E + (long long)ps.wout_col * (N / 8) : nullptr;
+    }
     lag = (DIM == 3 && stencil) ? 1 : 0;
     tpt = (DIM == 3) ? (stencil ? tl.ZS + 2 : tl.ZS) : 1;
     const int ntiles_cta = ((int)blockIdx.x < tl.ntiles) ? (tl.ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
