@@ -379,11 +379,24 @@ struct StreamEngine {
   // halo of the tile to the left, the right column the left halo of the next
   __device__ __forceinline__ void store_point(const STask& T, int zz, float* vc, float* ec, float x) const {
     vc[T.bx * TX + lx4 + g + gnx * (T.by * TY + ly) + gplane * zz] = x;
-    if (edge) {
+    if (ec && edge) {
       int nb = T.bx + edx;
       nb = nb < 0 ? gtx - 1 : (nb == gtx ? 0 : nb);
       ec[geplane * zz + (T.by * gtx + nb) * (2 * TY) + eoff] = x;   // edge_slot(nb, T.by, zz) + eoff
     }
+  }
+
+  // The x-halo copies of a projected plane (ring slot rs), written by one warp
+  // after the barrier: lanes 0-15 the tile's left column into the record of the
+  // tile to the left (its right halo), lanes 16-31 the right column into the
+  // record of the next tile (its left halo) -- two 64-byte rows.
+  __device__ __forceinline__ void x_edges(const STask& T, int rs) const {
+    const int zz = (DIM == 3) ? wrapi(T.z, e.P.op.nz) : 0;
+    const int side = e.lane >> 4, r = e.lane & (TY - 1);
+    const float v = ring[rs * SQ_RS + (r + 1) * SQ_RP + 4 + (side ? TX - 1 : 0)];
+    int nb = T.bx + (side ? 1 : -1);
+    nb = nb < 0 ? gtx - 1 : (nb == gtx ? 0 : nb);
+    ex[geplane * zz + (T.by * gtx + nb) * (2 * TY) + (side ? 0 : TY) + r] = v;
   }
 
   // x (quad) = a*src - sum_c coef_c V_c over this thread's column slots
@@ -460,7 +473,7 @@ struct StreamEngine {
     rg[(ly + 1) * SQ_RP + 4 + lx4 + g] = xg;
     if (T.main) {
       const int zz = (DIM == 3) ? wrapi(T.z, d.nz) : 0;
-      if (ps.xout_col >= 0) store_point(T, zz, vx, ex, xg);
+      if (ps.xout_col >= 0) store_point(T, zz, vx, nullptr, xg);   // edges: x_edges
       if (!stencil && (ps.self & SELF_XX)) E::kahan(A.ss[0], A.sc[0], xg * xg);
     }
     if (has_halo(T)) {
@@ -531,6 +544,7 @@ struct StreamEngine {
       if (refill && e.tid == 0) expect(Ti, si);
       __syncthreads();
       if (ld_volatile_i32(s_stop)) break;
+      if (ex && T.main && e.warp == 0) x_edges(T, i & (SQ_NRING - 1));
       // the stage of task i-1-lag is free: refill it with task i+depth
       if (refill) issue(Ti, si);
       bool compute = stencil;
