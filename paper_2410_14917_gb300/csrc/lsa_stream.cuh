@@ -144,6 +144,7 @@ struct StreamEngine {
   // record of the tile edx away (left for lx = 0, right for lx = TX-1) at eoff
   const bool edge;
   const int edx, eoff;
+  const int hring;          // ring offset of this thread's halo point (halo_ring(q))
   // geometry in 32-bit units (a column has fewer than 2^31 points): row pitch,
   // plane size, tiles per row, edge-record plane size
   const int gnx, gplane, gtx, geplane;
@@ -154,7 +155,8 @@ struct StreamEngine {
       : e(en), maps(m), sp(p), ring(rg), stages(st), full0(b), s_stop(stop), itab(tab), coef2(c2),
         q(en.warp * 8 + (en.lane & 7)), g(en.lane >> 3), ly(q >> 2), lx4((q & 3) * 4),
         edge(lx4 + g == 0 || lx4 + g == TX - 1), edx(lx4 + g == 0 ? -1 : 1),
-        eoff((lx4 + g == 0 ? TY : 0) + ly), gnx(en.P.op.nx), gplane(en.P.op.nx * en.P.op.ny),
+        eoff((lx4 + g == 0 ? TY : 0) + ly), hring(halo_ring(en.warp * 8 + (en.lane & 7))),
+        gnx(en.P.op.nx), gplane(en.P.op.nx * en.P.op.ny),
         gtx(en.P.tl.tiles_x), geplane(en.P.tl.tiles_x * en.P.tl.tiles_y * 2 * TY) {}
 
   __device__ __forceinline__ const float* stage(int s) const {
@@ -336,9 +338,6 @@ struct StreamEngine {
     return (h - 2 * TX - TY + 1) * SQ_RP + 4 + TX;
   }
 
-  __device__ __forceinline__ static float pick(const float4& v, int i) {
-    return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
-  }
   __device__ __forceinline__ static float4 lds4(const float* p) {
     return *reinterpret_cast<const float4*>(p);
   }
@@ -367,6 +366,18 @@ struct StreamEngine {
   }
   __device__ __forceinline__ static ulonglong2 lds2x2(const float* p) {
     return *reinterpret_cast<const ulonglong2*>(p);
+  }
+  // Sum of the quad over the four column groups, component g to lane group g,
+  // in the butterfly's order (pairs across lane bit 3, then across bit 4), so
+  // a point's value equals bit for bit what bfly gives its halo copy.
+  __device__ __forceinline__ float quad_sum(const float4& x) const {
+    const bool b0 = g & 1, b1 = g & 2;
+    // across bit 3: keep the components whose low index bit is g's, send the others
+    const float s0 = b0 ? x.x : x.y, s1 = b0 ? x.z : x.w;
+    const float k0 = (b0 ? x.y : x.x) + __shfl_xor_sync(0xffffffffu, s0, 8);
+    const float k1 = (b0 ? x.w : x.z) + __shfl_xor_sync(0xffffffffu, s1, 8);
+    // across bit 4: keep component g
+    return (b1 ? k1 : k0) + __shfl_xor_sync(0xffffffffu, b1 ? k0 : k1, 16);
   }
   __device__ __forceinline__ static float bfly(float v) {
     v += __shfl_xor_sync(0xffffffffu, v, 8);
@@ -468,7 +479,7 @@ struct StreamEngine {
     const bool full = is_full(T);
     const float4 x = full ? proj_quad_n<SQ_COLH>(st + (ly + 1) * TX + lx4, a)
                           : proj_quad_n<SQ_COL>(st + ly * TX + lx4, a);
-    const float xg = pick(make_float4(bfly(x.x), bfly(x.y), bfly(x.z), bfly(x.w)), g);
+    const float xg = quad_sum(x);
     float* rg = ring + rs * SQ_RS;
     rg[(ly + 1) * SQ_RP + 4 + lx4 + g] = xg;
     if (T.main) {
@@ -487,7 +498,7 @@ struct StreamEngine {
         hx = proj_point_n<SQ_EW>(st + offE() + (q - 2 * TX), n, a);
       }
       hx = bfly(hx);
-      if (g == 0) rg[halo_ring(q)] = hx;
+      if (g == 0) rg[hring] = hx;
     }
   }
 
