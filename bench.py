@@ -48,7 +48,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # The 3D line's capture is of the 160^3 case, scaled by the unknowns (4.096x)
 # (profiles/k_arnoldi_stream_adr3d_160_fp32.md).
 PROFILED_TRAFFIC = {("grayscott2d_512", "fp64", "hcwy"): 9.090663e9 + 0.768122e9,
-                    ("adr3d_256", "fp32", "hcwy"): (16.758949e9 + 1.468831e9) * (256 / 160) ** 3}
+                    ("adr3d_256", "fp32", "hcwy"): (16.764652e9 + 1.468302e9) * (256 / 160) ** 3}
 
 
 def parse():
