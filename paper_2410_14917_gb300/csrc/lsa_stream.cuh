@@ -18,21 +18,26 @@
 //  * A task's boxes are issued by lane 0 of each warp (one box per warp, the
 //    TMA unit then works through them) right after the barrier that frees the
 //    stage, `depth` tasks ahead of the one being computed; thread 0 registers
-//    the byte count on the stage's mbarrier before that barrier.  The stages form a ring whose depth is chosen per
-//    pass from the shared memory left (up to 8 stages), so short passes
-//    (small j) keep as many bytes in flight as long ones.
+//    the byte count on the stage's mbarrier before that barrier.  The stages
+//    form a ring whose depth is chosen per pass from the shared memory left
+//    (up to 8 stages), so short passes (small j) keep as many bytes in flight
+//    as long ones.
 //  * Thread (q, g) owns a 4-point quad q of the tile and the columns
-//    c = g, g+4, g+8, ...: 128-bit shared loads, four independent FMA chains,
-//    and a two-step butterfly that leaves the projected quad in all four
-//    lanes.  The inner loops are instantiated per column count (no
-//    per-column branches); column slots past n read the source slot with a
-//    zero coefficient.  The 64 halo points use the same per-lane column split and
-//    the same summation order, so a halo value equals, bit for bit, the value
-//    the owning tile stores.
+//    c = g, g+4, g+8, ...: 128-bit shared loads, packed float32 pairs
+//    (fma.rn.f32x2), and a three-shuffle transpose reduction that leaves point
+//    g of the quad in lane group g.  The inner loops are unrolled to 16 column
+//    slots with an exit after the pass's count; column slots past n read the
+//    source slot with a zero coefficient.  The 64 halo points use the same
+//    per-lane column split and the same summation order (a butterfly pairing
+//    the same lanes in the same order), so a halo value equals, bit for bit,
+//    the value the owning tile stores.
 //  * The stencil of plane z needs the projection of plane z+1, so its inner
 //    products are formed one task later; the stage of plane z is kept until
 //    then.  Projected planes sit in a four-slot ring in shared memory; one
 //    __syncthreads per task separates the projection from the stencil.
+//  * Values are stored with per-pass column pointers and 32-bit indices; the
+//    x-halo copies of a projected plane are written after the barrier by one
+//    warp as two coalesced 64-byte rows read back from the ring.
 //
 // Every wait is bounded (globaltimer); on expiry the CTA sets the abort flag
 // and LSA_ERR_TIMEOUT, lets its own copies in flight land (bounded), and leaves.
