@@ -6,10 +6,12 @@
 // optionally applies the stencil (w = A x, needing the projection on a
 // one-point halo, recomputed redundantly by each tile), and accumulates inner
 // products of basis columns with x and/or w.  The per-CTA partial sums go to
-// global memory, and one grid barrier reduces them: the CTA that arrives last
-// sums the partials in a fixed order (deterministic) and does the small
-// O(j^2) double-precision work of the step (H column, correction matrix T,
-// norm estimate) before releasing the others.  A global reduction of the paper
+// global memory, and one grid barrier reduces them in two levels: the last CTA
+// of each group of RG CTAs sums its group, the last group sums the group rows
+// (both in a fixed order: deterministic) and does the small O(j^2)
+// double-precision work of the step (H column, correction matrix T, norm
+// estimate) before releasing the others.  (The batched form, whose groups are
+// instances, sums all its CTAs' partials in one level.)  A global reduction of the paper
 // (an MPI_Allreduce, Sect. 2.3) is therefore one grid barrier here.
 #pragma once
 
