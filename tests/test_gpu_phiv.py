@@ -10,8 +10,9 @@ import pytest
 
 import workloads as W
 from oracle import exact as OE
+from oracle import krylov as OK
 from oracle import operators as OP
-from tests.gpu_util import FP32_TOL, FP64_TOL, device_inputs, oracle_phiv, rel_errors
+from tests.gpu_util import FP32_TOL, FP64_TOL, device_inputs, expected_syncs, oracle_phiv, rel_errors
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -114,3 +115,35 @@ def test_barrier_timeout_returns_error_and_context_survives():
     y, st, inp = run(cfg, "hcwy", "fp64")                  # the context is still usable
     ref, _ = oracle_phiv(cfg)
     assert max(rel_errors(y, ref)) < FP64_TOL
+
+
+def test_norm_estimate_fallback_path():
+    """A diagonal operator (3D ADR with no diffusion or advection) with three
+    eigenvalue clusters of width 1e-11: the Krylov space is nearly exhausted
+    after three steps, the Pythagorean radicand of Eq. 18 goes negative and
+    Alg. 4 falls back to an explicit norm (one extra reduction each time).
+    The result still matches the oracle, and the sync count includes them
+    (after a detected breakdown there is no final reduction)."""
+    import paper_2410_14917_gb300 as lsa
+    from oracle import operators as OPS
+
+    n, m, p, h = 16, 10, 1, 0.5
+    rng = np.random.default_rng(6)
+    r = rng.choice([-1.0, -0.5, 0.0], n ** 3) + 1e-11 * rng.standard_normal(n ** 3)
+    b = rng.uniform(-1, 1, n ** 3)
+    A = OPS.adr3d(n, n, n, 1.0 / n, 0.0, (0.0, 0.0, 0.0), r)
+    ref, _ = OK.phiv(lambda x: A @ x, b, h, p, m, "mgs")
+    op = lsa.Operator.adr3d(n, n, n, 1.0 / n, 0.0, (0.0, 0.0, 0.0), torch.from_numpy(r).cuda())
+    degenerate = 0
+    for variant in ("hcwy", "hncwy", "hgsmgs"):
+        y, st = lsa.phiv(op, torch.from_numpy(b).cuda(), h, p, m, variant=variant)
+        assert max(rel_errors(y, ref)) < FP64_TOL, variant
+        f = st["norm_fallbacks"]
+        if st["breakdown"]:
+            # detected at step j: by the estimate (m_eff = j) or lagged (m_eff = j - 1);
+            # no final reduction after a breakdown
+            assert st["grid_syncs"] - f in (st["m_eff"], st["m_eff"] + 1)
+        else:
+            assert st["grid_syncs"] == expected_syncs(variant, st["m_eff"], f)
+        degenerate += f + st["breakdown"]
+    assert degenerate >= 1     # the fallback (or the breakdown it leads to) was taken
