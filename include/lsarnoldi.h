@@ -264,7 +264,12 @@ lsa_status lsa_expm_phi(const double* H, int ldh, int m, double h, int p, double
  *  last call's contents (each call re-initialises what must start at zero), so
  *  calls whose work overlaps on the GPU -- on different streams, or from
  *  different host threads -- race and must be serialised by the caller.
- *  The call allocates nothing (no cudaMalloc/cudaFree, no event creation). */
+ *  The call allocates nothing (no cudaMalloc/cudaFree, no event creation);
+ *  since it records no events, the stats it fills (when non-NULL) report
+ *  ms_arnoldi, ms_expm, ms_combine, launches and arnoldi_kernel as 0 -- the
+ *  status, m_eff, breakdown, fallback, sync and scalar fields are as lsa_phiv's.
+ *  After cudaDeviceReset on a device, do not call it on that device again in
+ *  the same process (the device address it cached belongs to the old context). */
 lsa_status lsa_phiv_noalloc(const lsa_op* op, const double* v, double h, int p, int m, double tol,
                             int variant, int precision, double* y, lsa_stats* stats,
                             void* stream);

@@ -24,6 +24,12 @@ residual r = phi_1(hA)v - y_t:
                forced linear ODE).  So a = top half of phi_1(hK)[0; v]: one more
                phi-product, on a 2N-sized block operator.
 
+  dL/dF      (closed form) dA/dF = -I commutes with A, so d/dF phi_1(hA)v =
+               -h phi_1'(hA) v, and term by term in the series of Eq. 6
+               phi_1'(z) = sum_j (j+1) z^j / (j+2)! = phi_1(z) - phi_2(z):
+               dL/dF = -h r . (phi_1(hA)v - phi_2(hA)v), read off one phi
+               product with p = 2 (``dF_closed_form``).
+
 ``grads_krylov`` evaluates these with O-Krylov (``krylov.phiv``);
 ``grads_dense`` evaluates the same derivatives for tiny N with no Krylov step
 and no closed form: dense exponentials of the Eq. 7 matrix and
@@ -64,8 +70,17 @@ def loss(A, v, y_t, h, m, variant="mgs"):
     return 0.5 * float(r @ r), y
 
 
-def grads_krylov(A, dA, v, y_t, h, m, variant="mgs"):
-    """L, y = (phi_0, phi_1)(hA)v and the gradients, each by O-Krylov with m steps."""
+def dF_closed_form(A, v, r, h, m, variant="mgs"):
+    """dL/dF = -h r . (phi_1(hA)v - phi_2(hA)v) by O-Krylov with m steps (the
+    closed form above; pinned against the Frechet form and dense expm_frechet)."""
+    y, _ = phiv(lambda x: A @ x, v, h, 2, m, variant)
+    return -h * float(r @ (y[1] - y[2]))
+
+
+def grads_krylov(A, dA, v, y_t, h, m, variant="mgs", f_closed=False):
+    """L, y = (phi_0, phi_1)(hA)v and the gradients, each by O-Krylov with m
+    steps.  dL/dtheta uses the block-operator (Frechet) product for every
+    component, or, with f_closed, the closed form for the F component."""
     L, y = loss(A, v, y_t, h, m, variant)
     r = y[1] - y_t
     At = A.T.tocsr()
@@ -75,7 +90,10 @@ def grads_krylov(A, dA, v, y_t, h, m, variant="mgs"):
     N = v.size
     z0 = np.concatenate([np.zeros(N), v])
     g_t = []
-    for E in dA:
+    for k, E in enumerate(dA):
+        if f_closed and THETA[k] == "F":
+            g_t.append(dF_closed_form(A, v, r, h, m, variant))
+            continue
         K = sp.bmat([[A, E], [None, A]], format="csr")
         yk, _ = phiv(lambda x: K @ x, z0, h, 1, m, variant)
         g_t.append(float(r @ yk[1][:N]))

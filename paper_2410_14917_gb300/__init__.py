@@ -156,13 +156,28 @@ def arnoldi(op: Operator, v: torch.Tensor, m: int, variant="hcwy", precision="fp
     return V.T, H.T, (s.as_dict() if stats else None)
 
 
+def _check_vector_and_output(v: torch.Tensor, p: int, y):
+    """v: contiguous float64 on the current CUDA device (the library launches on
+    the current device); y, when given, a contiguous float64 (p+1, N) tensor on
+    the same device.  Returns y (allocated when None)."""
+    if v.dtype != torch.float64 or not v.is_cuda or not v.is_contiguous():
+        raise ValueError("v must be a contiguous float64 CUDA tensor")
+    if v.device.index != torch.cuda.current_device():
+        raise ValueError(f"v is on {v.device}, but cuda:{torch.cuda.current_device()} is the current device")
+    N = v.numel()
+    if y is None:
+        return torch.empty((p + 1, N), dtype=torch.float64, device=v.device)
+    if (y.dtype != torch.float64 or y.device != v.device or not y.is_contiguous()
+            or tuple(y.shape) != (p + 1, N)):
+        raise ValueError(f"y must be a contiguous float64 ({p + 1}, {N}) tensor on {v.device}")
+    return y
+
+
 def phiv(op: Operator, v: torch.Tensor, h: float, p: int, m: int, tol: float = 0.0,
          variant="hcwy", precision="fp64", y=None, work=None, stream=None, stats=True):
     """y[k] = phi_k(h A) v for k = 0..p; returns (y, stats dict or None)."""
-    if v.dtype != torch.float64 or not v.is_cuda or not v.is_contiguous():
-        raise ValueError("v must be a contiguous float64 CUDA tensor")
+    y = _check_vector_and_output(v, p, y)
     N = v.numel()
-    y = torch.empty((p + 1, N), dtype=torch.float64, device=v.device) if y is None else y
     work = work or Workspace.for_call(op, min(m, N), p, precision)
     s = LsaStats()
     st = B.lib().lsa_phiv(ctypes.byref(op.c), _ptr(v), float(h), int(p), int(m), float(tol),
@@ -235,10 +250,7 @@ def phiv_noalloc(op: Operator, v: torch.Tensor, h: float, p: int, m: int, tol: f
                  variant="hcwy", precision="fp64", y=None, stream=None, stats=True):
     """phiv through lsa_phiv_noalloc: the library's fixed static device workspace
     is used instead of a caller-provided one (for callers that cannot allocate)."""
-    if v.dtype != torch.float64 or not v.is_cuda or not v.is_contiguous():
-        raise ValueError("v must be a contiguous float64 CUDA tensor")
-    N = v.numel()
-    y = torch.empty((p + 1, N), dtype=torch.float64, device=v.device) if y is None else y
+    y = _check_vector_and_output(v, p, y)
     s = LsaStats()
     st = B.lib().lsa_phiv_noalloc(ctypes.byref(op.c), _ptr(v), float(h), int(p), int(m), float(tol),
                                   VARIANTS[variant], PRECISIONS[precision], _ptr(y),

@@ -13,7 +13,13 @@
 // device memory, so the device address is looked up once per device with
 // cudaGetSymbolAddress (with that device current) and cached.  The entry point
 // itself then calls the regular lsa_phiv with that address as its workspace,
-// with no event creation and no allocation of any kind.
+// with no event creation and no allocation of any kind.  The cached address
+// belongs to the device's current context: after cudaDeviceReset (or a release
+// and re-creation of the primary context) the library's module is loaded
+// again and the cache must not be used, so a process that resets a device
+// must not call this entry point afterwards.
+#include <atomic>
+
 #include "lsa_internal.cuh"
 
 namespace {
@@ -23,7 +29,9 @@ constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) unsigned char g_lsa_static_work[kStaticBytes];
 
-void* g_static_addr[kMaxDevices];   // device address of g_lsa_static_work, per device
+// device address of g_lsa_static_work, per device (first calls from several
+// host threads may all look it up; they store the same value)
+std::atomic<void*> g_static_addr[kMaxDevices];
 
 }  // namespace
 
@@ -33,11 +41,11 @@ extern "C" lsa_status lsa_phiv_noalloc(const lsa_op* op, const double* v, double
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return LSA_ERR_CUDA;
   if (dev < 0 || dev >= kMaxDevices) return LSA_ERR_ARG;
-  if (!g_static_addr[dev]) {          // first call on this device: look the array up
-    void* addr = nullptr;
-    if (cudaGetSymbolAddress(&addr, g_lsa_static_work) != cudaSuccess || !addr)
+  void* work = g_static_addr[dev].load(std::memory_order_acquire);
+  if (!work) {                        // first call on this device: look the array up
+    if (cudaGetSymbolAddress(&work, g_lsa_static_work) != cudaSuccess || !work)
       return LSA_ERR_CUDA;
-    g_static_addr[dev] = addr;
+    g_static_addr[dev].store(work, std::memory_order_release);
   }
   const long long N = lsa_op_dof(op);
   if (N < 1 || m < 1) return LSA_ERR_ARG;
@@ -45,7 +53,6 @@ extern "C" lsa_status lsa_phiv_noalloc(const lsa_op* op, const double* v, double
   const size_t need = lsa_workspace_bytes(op, m_used, p, precision);
   if (need == 0) return LSA_ERR_ARG;
   if (need > kStaticBytes) return LSA_ERR_WORKSPACE;   // beyond the fixed maximum
-  void* work = g_static_addr[dev];
   lsa_status st = lsa_phiv(op, v, h, p, m, tol, variant, precision, y, work, kStaticBytes,
                            nullptr, stream);
   if (st != LSA_OK) return st;

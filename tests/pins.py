@@ -332,9 +332,35 @@ def pin_sync_counts():
     bad += sum(s != 3 for s in r["syncs"])
     for var in ("hcwy", "hncwy", "hgsmgs"):
         r = OA.arnoldi(mv, inp["v"], m, var)
-        expect = [1 + (1 if j == m else 0) for j in range(1, m + 1)]
-        bad += sum((s - f) != e for s, e, f in zip(r["syncs"], expect, [0] * m)) if r["fallbacks"] == 0 else 0
+        bad += _hybrid_sync_mismatch(r, m)
+    # a case that takes the explicit-norm fallback: the per-step counts must
+    # still add up (one step charged 2, not 1) -- and the case must fall back
+    op, b, mf = fallback_problem()
+    for var in ("hcwy", "hncwy"):
+        r = OA.arnoldi(op, b, mf, var)
+        bad += _hybrid_sync_mismatch(r, mf) + (r["fallbacks"] < 1)
     return float(bad)
+
+
+def _hybrid_sync_mismatch(r, m):
+    """Alg. 4's count: one reduction at every step, one more at each step that
+    took the explicit-norm fallback, one more for the final norm when the
+    process ran all m steps.  Returns the number of mismatches (0 is good)."""
+    syncs, f = r["syncs"], r["fallbacks"]
+    full = r["m_eff"] == m and len(syncs) == m
+    expect = [1 + (1 if (full and j == len(syncs)) else 0) for j in range(1, len(syncs) + 1)]
+    extra = [s - e for s, e in zip(syncs, expect)]
+    return sum(x not in (0, 1) for x in extra) + (sum(extra) != f)
+
+
+def fallback_problem(n=12, seed=6):
+    """A diagonal operator with three eigenvalue clusters of width 1e-11: the
+    Krylov space is nearly exhausted after three steps and the Pythagorean
+    radicand of Eq. 18 goes negative (Alg. 4's explicit-norm fallback)."""
+    rng = np.random.default_rng(seed)
+    lam = rng.choice([-1.0, -0.5, 0.0], n ** 3) + 1e-11 * rng.standard_normal(n ** 3)
+    b = rng.uniform(-1, 1, n ** 3)
+    return (lambda x: lam * x), b, 10
 
 
 # --- adjoint (gradients of 1/2 ||phi_1(hA(theta))v - y_t||^2) ----------------
@@ -355,6 +381,24 @@ def pin_adjoint_vs_dense():
     rel = lambda a, b: float(np.max(np.abs(np.asarray(a) - np.asarray(b))) / np.max(np.abs(b)))
     return max(abs(gk["L"] - gd["L"]) / gd["L"], rel(gk["dv"], gd["dv"]), abs(gk["dh"] - gd["dh"]) / abs(gd["dh"]),
                rel(gk["dtheta"], gd["dtheta"]))
+
+
+def pin_adjoint_dF_closed_form():
+    """The closed form dL/dF = -h r.(phi_1 v - phi_2 v) against scipy's Frechet
+    derivative of exp along dA/dF (tiny grid, no Krylov truncation: m = the
+    full dimension) and against the Krylov block-operator product at the
+    adjoint test size (m = 40 on 32 x 32)."""
+    cfg, inp, A, dA = _adjoint_case()
+    gd = OAD.grads_dense(A, dA, inp["v"], inp["y_target"], cfg["h"])
+    r = gd["r"]
+    e1 = abs(OAD.dF_closed_form(A, inp["v"], r, cfg["h"], cfg["m"]) - gd["dtheta"][2]) / abs(gd["dtheta"][2])
+    cfg2 = W.grayscott2d(32, Du=2e-3, Dv=1e-3, h=0.5, p=1, m=40, seed=101)
+    inp2 = W.adjoint_inputs(cfg2)
+    A2, dA2 = OAD.grayscott_parts(cfg2, inp2)
+    gf = OAD.grads_krylov(A2, dA2, inp2["v"], inp2["y_target"], cfg2["h"], 40)
+    gc = OAD.grads_krylov(A2, dA2, inp2["v"], inp2["y_target"], cfg2["h"], 40, f_closed=True)
+    e2 = abs(gc["dtheta"][2] - gf["dtheta"][2]) / abs(gf["dtheta"][2])
+    return max(e1, e2)
 
 
 def pin_adjoint_finite_differences(n=8, eps=1e-6, m=60):

@@ -27,8 +27,10 @@ def make(cfg, u0, m=30, nsub=1, variant="hcwy"):
 
 
 def rel(a, b):
+    """The larger of the normwise and the element-wise (max-abs over max-abs) error."""
     a = a.detach().cpu().numpy() if hasattr(a, "detach") else np.asarray(a)
-    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    b = np.asarray(b)
+    return float(max(np.linalg.norm(a - b) / np.linalg.norm(b), np.max(np.abs(a - b)) / np.max(np.abs(b))))
 
 
 def test_rhs_kernel_matches_oracle():

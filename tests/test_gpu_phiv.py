@@ -134,7 +134,6 @@ def test_norm_estimate_fallback_path():
     A = OPS.adr3d(n, n, n, 1.0 / n, 0.0, (0.0, 0.0, 0.0), r)
     ref, _ = OK.phiv(lambda x: A @ x, b, h, p, m, "mgs")
     op = lsa.Operator.adr3d(n, n, n, 1.0 / n, 0.0, (0.0, 0.0, 0.0), torch.from_numpy(r).cuda())
-    degenerate = 0
     for variant in ("hcwy", "hncwy", "hgsmgs"):
         y, st = lsa.phiv(op, torch.from_numpy(b).cuda(), h, p, m, variant=variant)
         assert max(rel_errors(y, ref)) < FP64_TOL, variant
@@ -145,5 +144,5 @@ def test_norm_estimate_fallback_path():
             assert st["grid_syncs"] - f in (st["m_eff"], st["m_eff"] + 1)
         else:
             assert st["grid_syncs"] == expected_syncs(variant, st["m_eff"], f)
-        degenerate += f + st["breakdown"]
-    assert degenerate >= 1     # the fallback (or the breakdown it leads to) was taken
+        # each variant meets the degenerate case: the fallback, or the breakdown it leads to
+        assert f + st["breakdown"] >= 1, variant

@@ -80,3 +80,17 @@ def test_stream_kernel_arnoldi_relation():
     assert np.linalg.norm(G - np.eye(m + 1)) < 1e-4
     R = (A @ V[:, :m]) - V @ H
     assert np.linalg.norm(R) / np.linalg.norm(A @ V[:, :m]) < 1e-5
+
+
+@pytest.mark.parametrize("n", [128, 256])
+def test_stream_kernel_large_grids_match_oracle(n):
+    """The 3D ADR workload's kernel at 128^3 and at the full 256^3 (m = 40):
+    many z-segments per tile column, every pass's stage ring at its working
+    depth, against the oracle (its H-CWY form, which the oracle pins equal to
+    MGS) element by element."""
+    cfg = W.adr3d(n, m=40, p=1) if n != 256 else W.config(2)
+    y_s, st_s = run(cfg, "hcwy", True)
+    assert st_s["arnoldi_kernel"] == 2 and st_s["m_eff"] == 40
+    ref, info = oracle_phiv(cfg, "hcwy")
+    assert max(rel_errors(y_s, ref)) < FP32_TOL
+    assert st_s["grid_syncs"] == cfg["m"] + 1 + st_s["norm_fallbacks"]

@@ -8,5 +8,9 @@ def test_adjoint_krylov_matches_dense_frechet():
     assert pins.pin_adjoint_vs_dense() < 1e-9
 
 
+def test_adjoint_dF_closed_form_matches_frechet():
+    assert pins.pin_adjoint_dF_closed_form() < 1e-12
+
+
 def test_adjoint_matches_central_differences():
     assert pins.pin_adjoint_finite_differences() < 1e-5

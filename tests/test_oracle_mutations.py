@@ -114,6 +114,36 @@ def test_adjoint_derivative_sign_slip_is_caught(monkeypatch):
     assert pins.pin_adjoint_finite_differences() > 1e-3
 
 
+def test_adjoint_dF_closed_form_slips_are_caught(monkeypatch):
+    from oracle import adjoint as OAD
+    from oracle.krylov import phiv
+
+    def plus(A, v, r, h, m, variant="mgs"):                          # phi_1 + phi_2
+        y, _ = phiv(lambda x: A @ x, v, h, 2, m, variant)
+        return -h * float(r @ (y[1] + y[2]))
+    monkeypatch.setattr(OAD, "dF_closed_form", plus)
+    assert pins.pin_adjoint_dF_closed_form() > 1e-3
+
+    def no_h(A, v, r, h, m, variant="mgs"):                          # the factor h dropped
+        y, _ = phiv(lambda x: A @ x, v, h, 2, m, variant)
+        return -float(r @ (y[1] - y[2]))
+    monkeypatch.setattr(OAD, "dF_closed_form", no_h)
+    assert pins.pin_adjoint_dF_closed_form() > 1e-3
+
+
+def test_uncounted_fallback_reduction_is_caught(monkeypatch):
+    orig = OA.hybrid
+
+    def bad(matvec, b, m, variant="hcwy"):
+        r = orig(matvec, b, m, variant)
+        r["syncs"] = [min(s, 1) for s in r["syncs"]]                   # fallbacks and final uncharged
+        return r
+    monkeypatch.setattr(OA, "hybrid", bad)
+    for v in ("hcwy", "hncwy", "hgsmgs"):
+        monkeypatch.setitem(OA.VARIANTS, v, lambda f, b, m, v=v: bad(f, b, m, v))
+    assert pins.pin_sync_counts() > 0
+
+
 def test_iocgs_window_slip_is_caught(monkeypatch):
     orig = OA.iocgs
     monkeypatch.setattr(OA, "iocgs", lambda f, b, m, nprev=2: orig(f, b, m, nprev=1))

@@ -2,7 +2,13 @@
 memory (plugins inside an application that owns the device memory pool,
 latency-critical code that must not call cudaMalloc/cudaFree) -- gives the same
 phi products as lsa_phiv with a caller-provided workspace, on two calls in a
-row, through the C ABI.  Collected last on purpose."""
+row, through the C ABI.
+
+The file is collected last (its name sorts last) so that a run that stops at
+the first failure has run every other GPU test before this one.  No other test
+depends on it or on the order: the test passes alone in a fresh process and
+after the others (the static array is only touched here, and each call
+re-initialises what must start at zero)."""
 import ctypes
 
 import numpy as np
