@@ -601,3 +601,29 @@ def pin_lincomb_adaptive(tol=1e-10, tau=2.0, m=12):
     u, info = OL.lincomb_adaptive(lambda x: A @ x, bs, tau, m, tol)
     err = float(np.linalg.norm(u - ref) / np.linalg.norm(ref))
     return err / tol, len(info["sizes"]), info["converged"]
+
+
+def pin_lincomb_adaptive_m(tol=1e-10, tau=2.0):
+    """Sub-steps with adaptive size and Krylov dimension (this build's rule) on
+    the stiff operator of ``pin_lincomb_adaptive``: started with a dimension far
+    too small (m0 = 4) the rule must raise it, started far too large (m0 = 40)
+    it must lower it; both results are within a small multiple of tol of the
+    dense augmented exponential and every accepted sub-step met the tolerance.
+    Returns a dict per start: error relative to tol, first/largest/last
+    dimension, sub-steps, converged, modeled cost against the fixed-m run."""
+    cfg = W.advdiff2d(12, diff=0.05, vel=(1.0, 0.5))
+    A = OP.from_workload(cfg, {}).toarray()
+    rng = np.random.default_rng(25)
+    bs = [rng.uniform(-1, 1, A.shape[0]) for _ in range(3)]
+    ref = OE.phi_combination_dense(A, bs, tau, expm=scipy.linalg.expm)
+    out = {}
+    for m0 in (4, 40):
+        u, info = OL.lincomb_adaptive_m(lambda x: A @ x, bs, tau, m0, tol)
+        _, fixed = OL.lincomb_adaptive(lambda x: A @ x, bs, tau, m0, tol)
+        cost = sum(OL.projection_cost(d) for d in info["dims"])
+        cost_fixed = len(fixed["sizes"]) * OL.projection_cost(m0)
+        out[m0] = dict(err=float(np.linalg.norm(u - ref) / np.linalg.norm(ref)) / tol,
+                       first=info["dims"][0], largest=max(info["dims"]), last=info["dims"][-1],
+                       substeps=len(info["sizes"]), converged=info["converged"],
+                       cost_ratio=cost / cost_fixed)
+    return out

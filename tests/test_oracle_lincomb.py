@@ -25,3 +25,17 @@ def test_lincomb_adaptive_substeps_meet_the_tolerance():
     err_over_tol, nsteps, converged = pins.pin_lincomb_adaptive()
     assert converged and nsteps > 1
     assert err_over_tol < 10.0
+
+
+def test_lincomb_adaptive_dimension_grows_and_shrinks():
+    """Adaptive sub-step size and Krylov dimension (this build's rule): a start
+    far below the needed dimension is raised, one far above it is lowered,
+    both meet the tolerance against the dense augmented exponential, and the
+    modeled cost beats the fixed-m controller from the same start."""
+    r = pins.pin_lincomb_adaptive_m()
+    lo, hi = r[4], r[40]
+    assert lo["converged"] and hi["converged"]
+    assert lo["err"] < 10.0 and hi["err"] < 10.0
+    assert lo["largest"] >= 10                # raised from 4
+    assert hi["last"] <= 20                   # lowered from 40
+    assert lo["cost_ratio"] < 0.5 and hi["cost_ratio"] < 1.0

@@ -144,6 +144,36 @@ def test_uncounted_fallback_reduction_is_caught(monkeypatch):
     assert pins.pin_sync_counts() > 0
 
 
+def _adaptive_m_pin_fails():
+    r = pins.pin_lincomb_adaptive_m()
+    lo, hi = r[4], r[40]
+    ok = (lo["converged"] and hi["converged"] and lo["err"] < 10.0 and hi["err"] < 10.0
+          and lo["largest"] >= 10 and hi["last"] <= 20 and lo["cost_ratio"] < 0.5 and hi["cost_ratio"] < 1.0)
+    return not ok
+
+
+def test_adaptive_m_decay_sign_slip_is_caught(monkeypatch):
+    from oracle import lincomb as OL
+    orig = OL.plan_next
+
+    def bad(kappa, m, err, tol_abs, m_min, m_max, accepted):
+        return orig(None if kappa is None else 1.0 / kappa, m, err, tol_abs, m_min, m_max, accepted)
+    monkeypatch.setattr(OL, "plan_next", bad)
+    assert _adaptive_m_pin_fails()
+
+
+def test_adaptive_m_probe_index_slip_is_caught(monkeypatch):
+    from oracle import lincomb as OL
+    from oracle.krylov import small_phi_coeffs
+
+    def bad(info, dt, mp):                          # H_{mp,mp} instead of H_{mp+1,mp}
+        H = info["H"]
+        c = small_phi_coeffs(H[:mp, :mp], dt, 0)
+        return float(info["beta"]) * abs(dt) * float(H[mp - 1, mp - 1]) * abs(float(c[1][mp - 1]))
+    monkeypatch.setattr(OL, "estimate_at", bad)
+    assert _adaptive_m_pin_fails()
+
+
 def test_iocgs_window_slip_is_caught(monkeypatch):
     orig = OA.iocgs
     monkeypatch.setattr(OA, "iocgs", lambda f, b, m, nprev=2: orig(f, b, m, nprev=1))
