@@ -227,6 +227,38 @@ lsa_status lsa_phiv_lincomb_adaptive(const lsa_op* op, const double* b, int p, d
                                      double* u, double* scratch, void* work, size_t work_bytes,
                                      lsa_stats* stats, int* substeps, int* rejected, void* stream);
 
+/* lsa_phiv_lincomb_adaptive with the Krylov dimension of every sub-step
+ * adaptive as well as its size: Sect. 2.2 chooses both "as in KIOPS", whose
+ * formulas the paper does not give, so the rule is this library's own.  After
+ * a projection of dimension m over dt with estimate err (as in
+ * lsa_phiv_lincomb_adaptive), kappa -- the decay of the estimate per Krylov
+ * dimension -- is measured on the same projection (its estimate at dimension
+ * m - 2 costs one more small exponential); the error model
+ * err(dt', m') = err kappa^(m - m') (dt'/dt)^(m'+1) gives for every m' in
+ * [m_min, m_max] the size factor f(m') = 0.9 (tol beta / (err kappa^(m-m')))^(1/(m'+1))
+ * clamped to [0.2, 4], and the next sub-step takes the m' with the smallest
+ * modeled cost per unit of time (m'(m'+1)/2 + 3m') / f(m') -- the vectors one
+ * m'-step projection streams -- when that beats keeping m by 10 %.  After a
+ * rejection only m' >= m is considered and f is capped at 0.9.  Without a
+ * usable kappa (exact projection, breakdown, m < 3, kappa <= 1.05) only the
+ * size adapts.  Acceptance, the first size tau / nsub0 and the size floor are
+ * those of lsa_phiv_lincomb_adaptive.
+ *  m0         first dimension, clamped to [m_min, m_max];  1 <= m_min <= m_max
+ *             <= lsa_max_m() (m_max capped at N + p).
+ *  work       dev, lsa_lincomb_adaptive_m_workspace_bytes(op, m_max) bytes,
+ *             256-byte aligned.
+ *  dims       host, may be NULL when dims_cap = 0: the dimension of each
+ *             accepted sub-step, the first dims_cap of them.
+ *  Float64 form only; other arguments and the status as
+ *  lsa_phiv_lincomb_adaptive (the stream is synchronised after every
+ *  sub-step: the controller runs on the host). */
+size_t lsa_lincomb_adaptive_m_workspace_bytes(const lsa_op* op, int m_max);
+lsa_status lsa_phiv_lincomb_adaptive_m(const lsa_op* op, const double* b, int p, double tau, double tol,
+                                       int m0, int m_min, int m_max, int nsub0, int max_substeps,
+                                       int variant, double* u, double* scratch, void* work,
+                                       size_t work_bytes, lsa_stats* stats, int* substeps, int* rejected,
+                                       int* dims, int dims_cap, void* stream);
+
 /* Exponential-integrator building blocks (Sect. 4) besides the phi products.
  * lsa_rhs: f = F(u) for the Gray-Scott system whose Jacobian at a state is
  *   the LSA_OP_GRAYSCOTT2D operator: F(u, v) = [Du Lap u - u v^2 + F (1 - u);

@@ -233,6 +233,39 @@ def phiv_lincomb_adaptive(op: Operator, b: torch.Tensor, tau: float, m: int, tol
     return u, d
 
 
+def phiv_lincomb_adaptive_m(op: Operator, b: torch.Tensor, tau: float, m0: int, tol: float, m_min: int = 4,
+                            m_max: int = 64, nsub0: int = 1, max_substeps: int = 10000, variant="hcwy",
+                            u=None, work=None, stream=None):
+    """phiv_lincomb with the size and the Krylov dimension of every sub-step
+    adaptive (lsa_phiv_lincomb_adaptive_m); returns (u, stats dict with the
+    accepted and rejected sub-step counts and the dimension of each accepted one)."""
+    if b.dtype != torch.float64 or not b.is_cuda or not b.is_contiguous() or b.dim() != 2:
+        raise ValueError("b must be a contiguous (p+1, N) float64 CUDA tensor")
+    p = b.shape[0] - 1
+    N = b.shape[1]
+    u = torch.empty(N, dtype=torch.float64, device=b.device) if u is None else u
+    scratch = torch.empty(N, dtype=torch.float64, device=b.device)
+    if work is None:
+        nbytes = B.lib().lsa_lincomb_adaptive_m_workspace_bytes(ctypes.byref(op.c), int(m_max))
+        if nbytes == 0:
+            raise LsaError(B.LSA_ERR_ARG, "lsa_lincomb_adaptive_m_workspace_bytes")
+        work = Workspace(nbytes, device=b.device)
+    s = LsaStats()
+    nacc, nrej = ctypes.c_int(0), ctypes.c_int(0)
+    cap = int(max_substeps)
+    dims = (ctypes.c_int * cap)()
+    st = B.lib().lsa_phiv_lincomb_adaptive_m(ctypes.byref(op.c), _ptr(b), int(p), float(tau), float(tol),
+                                             int(m0), int(m_min), int(m_max), int(nsub0), cap,
+                                             VARIANTS[variant], _ptr(u), _ptr(scratch),
+                                             ctypes.c_void_p(work.ptr), work.nbytes, ctypes.byref(s),
+                                             ctypes.byref(nacc), ctypes.byref(nrej), dims, cap,
+                                             _stream_ptr(stream))
+    _check(st, "lsa_phiv_lincomb_adaptive_m")
+    d = s.as_dict()
+    d.update(substeps=nacc.value, rejected=nrej.value, dims=list(dims[:min(nacc.value, cap)]))
+    return u, d
+
+
 def axpby(a: float, x: torch.Tensor, b: float, y: torch.Tensor, out=None, stream=None):
     """out = a x + b y over float64 CUDA tensors of one size (lsa_axpby)."""
     for t_, name in ((x, "x"), (y, "y")):

@@ -58,6 +58,11 @@ SIGNATURES = {
                                           c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p,
                                           c_size_t, POINTER(LsaStats), POINTER(c_int), POINTER(c_int),
                                           c_void_p]),
+    "lsa_lincomb_adaptive_m_workspace_bytes": (c_size_t, [POINTER(LsaOp), c_int]),
+    "lsa_phiv_lincomb_adaptive_m": (c_int, [POINTER(LsaOp), c_void_p, c_int, c_double, c_double, c_int,
+                                            c_int, c_int, c_int, c_int, c_int, c_void_p, c_void_p,
+                                            c_void_p, c_size_t, POINTER(LsaStats), POINTER(c_int),
+                                            POINTER(c_int), POINTER(c_int), c_int, c_void_p]),
     "lsa_rhs": (c_int, [POINTER(LsaOp), c_void_p, c_void_p, c_void_p]),
     "lsa_axpby": (c_int, [c_longlong, c_double, c_void_p, c_double, c_void_p, c_void_p, c_void_p]),
     "lsa_expm_phi": (c_int, [c_void_p, c_int, c_int, c_double, c_int, c_void_p, c_void_p, c_size_t,

@@ -674,6 +674,228 @@ lsa_status lsa_phiv_lincomb_adaptive(const lsa_op* op, const double* b, int p, d
   return worst;
 }
 
+// Sub-steps with adaptive size and Krylov dimension (this library's rule):
+// after a projection of dimension m over dt with estimate err, the error model
+// err(dt', m') = err kappa^(m - m') (dt'/dt)^(m'+1) -- kappa, the decay of the
+// estimate per Krylov dimension, measured on the same projection between
+// m - kAdaptProbe and m -- gives for every m' the size factor
+// f(m') = 0.9 (tol beta / (err kappa^(m - m')))^(1/(m'+1)) in [0.2, 4], and the
+// next sub-step takes the m' of smallest modeled cost per unit of time
+// W(m') / f(m'), W(m) = m(m+1)/2 + 3m (vectors one m-step hybrid projection
+// streams), when it beats keeping m by 10 %.  After a rejection only m' >= m
+// is considered and f is capped at 0.9.  Without a usable kappa (exact
+// projection, breakdown, m - kAdaptProbe < 1, kappa <= 1.05) only the size
+// adapts, as in lsa_phiv_lincomb_adaptive.
+constexpr int kAdaptProbe = 2;
+constexpr double kKappaMin = 1.05;
+constexpr double kAdaptHyst = 0.9;
+
+static double adapt_cost(int m) { return 0.5 * m * (m + 1) + 3.0 * m; }
+
+static void adapt_plan(double kappa, int m, double err, double tol_abs, int m_min, int m_max, bool accepted,
+                       int* m_next, double* f_next) {
+  double f_keep = lincomb_step_factor(err, tol_abs, m);
+  if (!accepted && f_keep > 0.9) f_keep = 0.9;
+  *m_next = m;
+  *f_next = f_keep;
+  if (!(kappa > 0.0)) return;
+  const double keep = adapt_cost(m) / f_keep;
+  double best = keep, best_f = f_keep;
+  int best_m = m;
+  for (int mp = accepted ? m_min : m; mp <= m_max; ++mp) {
+    if (mp == m) continue;
+    double f = 0.9 * pow(tol_abs / (err * pow(kappa, (double)(m - mp))), 1.0 / (mp + 1));
+    f = f < 0.2 ? 0.2 : (f > 4.0 ? 4.0 : f);
+    if (!accepted && f > 0.9) f = 0.9;
+    const double c = adapt_cost(mp) / f;
+    if (c < best) { best = c; best_m = mp; best_f = f; }
+  }
+  if (best < kAdaptHyst * keep) { *m_next = best_m; *f_next = best_f; }
+}
+
+struct AdaptLayout {
+  size_t main, pctl, pc, total;
+};
+
+static bool adapt_layout(const lsa_op* op, int m_max, AdaptLayout* L) {
+  const size_t w = lsa_workspace_bytes(op, m_max, 0, LSA_FP64);
+  if (!w) return false;
+  L->main = 0;
+  L->pctl = align256(w);
+  L->pc = L->pctl + align256(sizeof(Ctl));
+  L->total = L->pc + align256((size_t)2 * (MMAX + 2) * sizeof(double));
+  return true;
+}
+
+size_t lsa_lincomb_adaptive_m_workspace_bytes(const lsa_op* op, int m_max) {
+  if (!op || op->kind > LSA_OP_ADR3D || m_max < 1 || m_max > MMAX) return 0;
+  AdaptLayout L;
+  return adapt_layout(op, m_max, &L) ? L.total : 0;
+}
+
+lsa_status lsa_phiv_lincomb_adaptive_m(const lsa_op* op, const double* b, int p, double tau, double tol,
+                                       int m0, int m_min, int m_max, int nsub0, int max_substeps,
+                                       int variant, double* u, double* scratch, void* work,
+                                       size_t work_bytes, lsa_stats* stats, int* substeps, int* rejected,
+                                       int* dims, int dims_cap, void* stream) {
+  if (!b || !u || !scratch || u == scratch) return LSA_ERR_ARG;
+  if (variant < LSA_MGS || variant > LSA_IOCGS) return LSA_ERR_ARG;
+  if (p < 0 || p > PMAX || !isfinite(tau) || !(tol > 0.0) || !isfinite(tol) || nsub0 < 1 ||
+      max_substeps < 1 || dims_cap < 0 || (dims_cap > 0 && !dims))
+    return LSA_ERR_ARG;
+  if (!op || op->kind > LSA_OP_ADR3D) return LSA_ERR_ARG;
+  if (m_min < 1 || m_max < m_min || m_max > MMAX || m0 < 1) return LSA_ERR_ARG;
+  const long long N = lsa_op_dof(op);
+  if (N < 1) return LSA_ERR_ARG;
+  if (m_max > N + p) m_max = (int)(N + p);
+  if (m_min > m_max) m_min = m_max;
+  int m = m0 < m_min ? m_min : (m0 > m_max ? m_max : m0);
+  AdaptLayout AL;
+  if (!adapt_layout(op, m_max, &AL)) return LSA_ERR_ARG;
+  if (!work || !aligned256(work) || work_bytes < AL.total) return LSA_ERR_WORKSPACE;
+  char* wbase = (char*)work;
+  Ctl* pctl = (Ctl*)(wbase + AL.pctl);       // the probe exponential's control block
+  double* pc = (double*)(wbase + AL.pc);     // ... and its coefficients (2 x (MMAX + 2))
+  cudaStream_t s = (cudaStream_t)stream;
+  lsa_stats acc;
+  memset(&acc, 0, sizeof(acc));
+  acc.m_eff = m_max;
+  const double* cur = b;
+  double t = 0.0, dt = tau / nsub0;
+  const double floor_dt = fabs(tau) * ldexp(1.0, -30);
+  int nacc = 0, nrej = 0;
+  bool done = false, converged = true;
+  lsa_status worst = LSA_OK;
+  while (nacc + nrej < max_substeps) {
+    const bool last = fabs(dt) >= fabs(tau - t);
+    if (last) dt = tau - t;
+    double* out = (u != cur) ? u : scratch;
+    Prepared pr;
+    lsa_status st = prepare(op, m, LSA_FP64, work, AL.pctl, &pr);   // layout of this sub-step's m
+    if (st != LSA_OK) return st;
+    ArnoldiParams P = pr.P;
+    P.vin = cur;
+    P.variant = variant;
+    P.write_vlast = 0;
+    P.naug = p;
+    P.baug = b;
+    P.aug_t = t;
+    CallTimer tm(stats != nullptr, s);
+    cudaError_t e = launch_init(P.ctl, pr.d, nullptr, nullptr, LSA_FP64, P.H, (m + 1) * m, P.vin, P.V, s);
+    tm.mark(0);
+    if (e == cudaSuccess) e = launch_arnoldi(P, LSA_FP64, pr.L.G, s);
+    tm.mark(1);
+    SmallParams S;
+    memset(&S, 0, sizeof(S));
+    S.H = P.H;
+    S.ldh = m + 1;
+    S.ctl_in = P.ctl;
+    S.ctl = P.ctl;
+    S.m = m;
+    S.p = 0;
+    S.h = dt;
+    S.mats = (double*)(pr.w + pr.L.small);
+    S.C = (double*)(pr.w + pr.L.coefs);
+    S.ldc = MMAX + 2;
+    S.scale_out = 1;
+    S.timeout_ns = kTimeoutNs;
+    S.tol = 0.0;
+    if (e == cudaSuccess) e = launch_expm(S, s);
+    tm.mark(2);
+    if (e == cudaSuccess) e = launch_combine(P.V, LSA_FP64, N, S.C, S.ldc, 0, P.ctl, out, s);
+    tm.mark(3);
+    if (e != cudaSuccess) return LSA_ERR_CUDA;
+    lsa_stats one;
+    lsa_status r = fill_stats(P.ctl, &one, s);   // the controller reads the estimate on the host
+    if (r < 0) {
+      if (stats) { acc.status = r; *stats = acc; }
+      return r;
+    }
+    acc.grid_syncs += one.grid_syncs;
+    acc.grid_barriers += one.grid_barriers;
+    acc.norm_fallbacks += one.norm_fallbacks;
+    acc.ms_arnoldi += tm.ms(0, 1);
+    acc.ms_expm += tm.ms(1, 2);
+    acc.ms_combine += tm.ms(2, 3);
+    acc.launches += 4;
+    const double err = one.breakdown ? 0.0 : one.err_est;
+    const double tol_abs = tol * one.beta;
+    const bool accept = err <= tol_abs || fabs(dt) <= floor_dt;
+    // kappa: the same projection's estimate at dimension mp = m - kAdaptProbe,
+    // beta dt H_{mp+1,mp} |e_mp^T phi_1(dt H_mp) e_1| (one more small exponential)
+    double kappa = 0.0;
+    const int mp = m - kAdaptProbe;
+    if (!one.breakdown && one.m_eff == m && err > 0.0 && mp >= 1) {
+      if (cudaMemsetAsync(pctl, 0, sizeof(Ctl), s) != cudaSuccess) return LSA_ERR_CUDA;
+      SmallParams Q;
+      memset(&Q, 0, sizeof(Q));
+      Q.H = P.H;
+      Q.ldh = m + 1;
+      Q.ctl_in = nullptr;
+      Q.ctl = pctl;
+      Q.m = mp;
+      Q.p = 0;
+      Q.h = dt;
+      Q.mats = S.mats;
+      Q.C = pc;
+      Q.ldc = MMAX + 2;
+      Q.scale_out = 0;
+      Q.timeout_ns = kTimeoutNs;
+      if (launch_expm(Q, s) != cudaSuccess) return LSA_ERR_CUDA;
+      acc.launches += 2;
+      double hsub = 0.0, phin = 0.0;
+      int pst = 0;
+      if (cudaMemcpyAsync(&hsub, P.H + mp + (size_t)(mp - 1) * (m + 1), sizeof(double), cudaMemcpyDeviceToHost,
+                          s) != cudaSuccess ||
+          cudaMemcpyAsync(&phin, pc + (MMAX + 2) + (mp - 1), sizeof(double), cudaMemcpyDeviceToHost, s) !=
+              cudaSuccess ||
+          cudaMemcpyAsync(&pst, &pctl->status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess)
+        return LSA_ERR_CUDA;
+      if (pst < 0) return (lsa_status)pst;
+      const double e_p = one.beta * fabs(dt) * hsub * fabs(phin);
+      if (e_p > err) {
+        const double k = pow(e_p / err, 1.0 / kAdaptProbe);
+        if (k > kKappaMin) kappa = k;
+      }
+    }
+    if (accept) {
+      if (err > tol_abs) converged = false;
+      cur = out;
+      if (dims && nacc < dims_cap) dims[nacc] = m;
+      ++nacc;
+      if (one.m_eff < acc.m_eff) acc.m_eff = one.m_eff;
+      acc.breakdown |= one.breakdown;
+      if (nacc == 1) acc.beta = one.beta;
+      if (one.err_est > acc.err_est) acc.err_est = one.err_est;
+      acc.h_last = one.h_last;
+      if (r == LSA_BREAKDOWN && worst == LSA_OK) worst = LSA_BREAKDOWN;
+      if (last) { done = true; break; }
+      t += dt;
+    } else {
+      ++nrej;
+    }
+    int m_next = m;
+    double f = 1.0;
+    adapt_plan(kappa, m, err, tol_abs, m_min, m_max, accept, &m_next, &f);
+    m = m_next;
+    dt *= f;
+  }
+  if (cur != u) {
+    if (cudaMemcpyAsync(u, cur, (size_t)N * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return LSA_ERR_CUDA;
+  }
+  if (!done || !converged) worst = LSA_NOT_CONVERGED;
+  if (substeps) *substeps = nacc;
+  if (rejected) *rejected = nrej;
+  if (stats) {
+    acc.status = worst;
+    acc.arnoldi_kernel = 0;
+    *stats = acc;
+  }
+  return worst;
+}
+
 lsa_status lsa_expm_phi(const double* H, int ldh, int m, double h, int p, double* C, void* work,
                         size_t work_bytes, void* stream) {
   if (!H || !C || m < 1 || m > MMAX || ldh < m || p < 0 || p > PMAX || !isfinite(h))

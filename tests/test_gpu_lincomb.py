@@ -195,3 +195,47 @@ def test_lincomb_adaptive_reports_the_substep_cap():
     lsa, op, A, b, bd = setup(cfg, p)
     u, st = lsa.phiv_lincomb_adaptive(op, bd, tau, m, tol, max_substeps=2)
     assert st["status"] == 2          # LSA_NOT_CONVERGED: tau not reached within the cap
+
+
+@pytest.mark.parametrize("name", ["grayscott2d", "adr3d"])
+@pytest.mark.parametrize("m0", [4, 40])
+def test_lincomb_adaptive_dimension_matches_oracle(name, m0):
+    """Sub-steps with adaptive size and Krylov dimension (this library's rule,
+    lsa_phiv_lincomb_adaptive_m) against the oracle running the same rule: the
+    result, the first accepted dimension, and the direction the dimension moves
+    from a start far too small (raised) or far too large (lowered)."""
+    p, tau, tol = 3, 2.0, 1e-10
+    cfg = case(name)
+    lsa, op, A, b, bd = setup(cfg, p)
+    ref, info = OL.lincomb_adaptive_m(lambda x: A @ x, list(b), tau, m0, tol)
+    u, st = lsa.phiv_lincomb_adaptive_m(op, bd, tau, m0, tol, variant="hcwy")
+    assert st["status"] == 0 and info["converged"]
+    assert rel(u, ref) < 20 * tol
+    assert st["dims"][0] == info["dims"][0]
+    assert len(st["dims"]) == st["substeps"] and abs(st["substeps"] - len(info["sizes"])) <= max(2, len(info["sizes"]) // 5)
+    if m0 == 4:
+        assert max(st["dims"]) >= 8
+    elif st["substeps"] > 1:
+        assert min(st["dims"]) <= 20
+
+
+def test_lincomb_adaptive_dimension_against_dense():
+    p, tau, tol = 2, 1.5, 1e-9
+    cfg = W.advdiff2d(16, m=12, diff=0.02)
+    lsa, op, A, b, bd = setup(cfg, p)
+    dense = OE.phi_combination_dense(A.toarray(), list(b), tau, expm=OE.scipy_expm)
+    u, st = lsa.phiv_lincomb_adaptive_m(op, bd, tau, 6, tol, m_min=3, m_max=32)
+    assert st["status"] == 0
+    assert rel(u, dense) < 20 * tol
+    assert all(3 <= d <= 32 for d in st["dims"])
+
+
+def test_lincomb_adaptive_dimension_rejects_bad_arguments():
+    import paper_2410_14917_gb300 as lsa
+    from paper_2410_14917_gb300 import LsaError
+
+    cfg = case("advdiff2d")
+    _, op, A, b, bd = setup(cfg, 1)
+    for kw in (dict(m_min=0), dict(m_min=10, m_max=5), dict(m_max=65)):
+        with pytest.raises(LsaError):
+            lsa.phiv_lincomb_adaptive_m(op, bd, 1.0, 8, 1e-8, **kw)
