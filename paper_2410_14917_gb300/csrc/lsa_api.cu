@@ -96,15 +96,31 @@ bool make_devop(const lsa_op* op, DevOp* d) {
   return true;
 }
 
+static int sm_count();
+
 Tiling make_tiling(const DevOp& d) {
   Tiling t;
   t.tiles_x = (d.nx + TX - 1) / TX;
   t.tiles_y = (d.ny + TY - 1) / TY;
-  // z-segment: the largest divisor of nz that is at most 32 (uniform segments)
+  // z-segment (3D): a divisor of nz (uniform segments), at least 4 and at most
+  // 64, that minimises the planes the busiest SM streams, tiles dealt
+  // round-robin to one CTA per SM: ceil(tiles / SMs) * (ZS + 2), the two being
+  // the segment's halo planes (longer segments: fewer halo planes; shorter
+  // ones: a smaller last round).  Ties go to the longer segment.
   t.ZS = 1;
-  if (d.kind == LSA_OP_ADR3D)
-    for (int z = (d.nz < 32 ? d.nz : 32); z >= 1; --z)
-      if (d.nz % z == 0) { t.ZS = z; break; }
+  if (d.kind == LSA_OP_ADR3D) {
+    const int sms = sm_count();
+    const long long txy = (long long)t.tiles_x * t.tiles_y;
+    long long best = -1;
+    for (int z = (d.nz < 64 ? d.nz : 64); z >= 1; --z) {
+      if (d.nz % z != 0 || (z < 4 && z != d.nz)) continue;
+      const long long tiles = txy * (d.nz / z);
+      const long long rounds = sms > 0 ? (tiles + sms - 1) / sms : tiles;
+      const long long cost = rounds * (z + 2);
+      if (best < 0 || cost < best) { best = cost; t.ZS = z; }
+    }
+    if (best < 0) t.ZS = d.nz;
+  }
   t.zsegs = (d.nz + t.ZS - 1) / t.ZS;
   t.ntiles = t.tiles_x * t.tiles_y * t.zsegs;
   return t;
