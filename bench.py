@@ -422,10 +422,11 @@ def bench_batched(args, world, rank, local, bcfg):
     gbs = byts / (ms_step / 1e3) / 1e9
     if args.precision == "fp64":
         achieved = flops / (ms_step / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+        pk64, pk64_src = fp64_peak(lsa)
+        roof = {"bound": "alu", "achieved": achieved, "peak": pk64, "unit": "TFLOP/s",
+                "frac": achieved / pk64, "traffic": None,
                 "kernel": "k_batched (persistent batched phi products; step time incl. its init kernel)",
-                "peak_source": "FP64 FMA pipe from unit counts and max clock (152 SMs x 2 FMA/clk x 2.07 GHz)",
+                "peak_source": pk64_src,
                 "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak, "algorithmic_bytes": byts,
                 "algorithmic_flops": flops}
     else:
@@ -570,10 +571,11 @@ def bench_adjoint(args, world, rank, local, cfg):
     ms_step = tot_ms / args.steps
     flops = adjoint_flops(cfg, m)
     achieved = flops / (ms_step / 1e3) / 1e12
-    roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+    pk64, pk64_src = fp64_peak(lsa)
+    roof = {"bound": "alu", "achieved": achieved, "peak": pk64, "unit": "TFLOP/s",
+            "frac": achieved / pk64, "traffic": None,
             "kernel": "whole gradient evaluation (five k_arnoldi launches with their small kernels)",
-            "peak_source": "FP64 FMA pipe from unit counts and max clock (152 SMs x 2 FMA/clk x 2.07 GHz)",
+            "peak_source": pk64_src,
             "algorithmic_flops": flops}
     line = {"metric": METRIC, "value": value, "unit": "grad/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
@@ -625,6 +627,7 @@ def bench_integrator(args, world, rank, local, cfg):
     import numpy as np
     import torch
 
+    import paper_2410_14917_gb300 as lsa
     import workloads as W
     from paper_2410_14917_gb300.integrators import GrayScottIntegrator
 
@@ -700,10 +703,11 @@ def bench_integrator(args, world, rank, local, cfg):
 
     byts, flops = algorithmic_counts(cfg, "fp64", m)
     achieved = flops / (ms_step / 1e3) / 1e12
-    roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+    pk64, pk64_src = fp64_peak(lsa)
+    roof = {"bound": "alu", "achieved": achieved, "peak": pk64, "unit": "TFLOP/s",
+            "frac": achieved / pk64, "traffic": None,
             "kernel": "whole EPI4 step (augmented-operator k_arnoldi with its small kernels)",
-            "peak_source": "FP64 FMA pipe from unit counts and max clock (152 SMs x 2 FMA/clk x 2.07 GHz)",
+            "peak_source": pk64_src,
             "algorithmic_flops": flops}
     line = {"metric": METRIC, "value": value, "unit": "integrator steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
@@ -796,6 +800,77 @@ def cpu_baseline(cfg, variant, budget):
             "sample": f"{n} full phiv call(s) of {cfg['name']} ({variant}, float64 NumPy/SciPy)"}, y
 
 
+def fp64_peak(lsa):
+    """(TFLOP/s, source) of the float64 roofline: the FMA throughput measured
+    on this GPU by lsa_probe_fp64_fma, else the nominal unit counts."""
+    meas = lsa.probe_fp64_fma_tflops()
+    if meas > 0:
+        return meas, ("measured float64 FMA throughput (lsa_probe_fp64_fma, CUDA events, best of 10 after a warm-up; "
+                      "nominal 152 SMs x 2 FMA/clk x 2.07 GHz = %.3f TFLOP/s)" % FP64_PEAK_TFLOPS)
+    return FP64_PEAK_TFLOPS, "nominal unit counts (152 SMs x 2 FMA/clk x 2.07 GHz)"
+
+
+def phiv_roofline(cfg, precision, variant, ms_a, m_eff, kernel_kind, fp64_peak, fp64_peak_src):
+    """Roofline object of the persistent Arnoldi kernel of one phiv call."""
+    byts, flops = algorithmic_counts(cfg, precision, m_eff)
+    hbm_peak, peak_kind = load_peaks()
+    if precision == "fp64":
+        achieved = flops / (ms_a / 1e3) / 1e12
+        return {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak,
+                "traffic": PROFILED_TRAFFIC.get((cfg["name"], precision, variant)),
+                "kernel": "k_arnoldi (persistent hybrid Arnoldi)",
+                "peak_source": fp64_peak_src,
+                "hbm_gbs": byts / (ms_a / 1e3) / 1e9, "hbm_frac": byts / (ms_a / 1e3) / 1e9 / hbm_peak,
+                "algorithmic_bytes": byts, "algorithmic_flops": flops}
+    achieved = byts / (ms_a / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+            "frac": achieved / hbm_peak,
+            "traffic": PROFILED_TRAFFIC.get((cfg["name"], precision, variant)),
+            "kernel": {0: "k_arnoldi", 1: "k_arnoldi_tma", 2: "k_arnoldi_stream"}[kernel_kind]
+                      + " (persistent Arnoldi, float32 basis)",
+            "peak_source": f"{peak_kind} hbm_gbs",
+            "algorithmic_bytes": byts, "algorithmic_flops": flops}
+
+
+def time_phiv(lsa, torch, cfg, precision, variant, steps, warmup, dev, flush, stream):
+    """Inputs resident on the device, `warmup` untimed calls, then `steps`
+    calls each bracketed by CUDA events on the launching stream (L2 flushed
+    before each).  Returns a dict with the per-call times, the library's own
+    per-kernel times, the first call's statistics and the device buffers."""
+    import workloads as W
+
+    inp = W.make_inputs(cfg)
+    N = W.n_dof(cfg)
+    p, m, h = cfg["p"], cfg["m"], cfg["h"]
+    fields = {k: torch.from_numpy(v).to(dev) for k, v in inp.items() if k != "v"}
+    v_host = torch.from_numpy(inp["v"]).pin_memory()
+    v = v_host.to(dev)
+    op = lsa.Operator.from_workload(cfg, fields)
+    work = lsa.Workspace.for_call(op, m, p, precision)
+    y = torch.empty((p + 1, N), dtype=torch.float64, device=dev)
+    _, st0 = lsa.phiv(op, v, h, p, m, variant=variant, precision=precision, y=y, work=work)
+    for _ in range(warmup):
+        lsa.phiv(op, v, h, p, m, variant=variant, precision=precision, y=y, work=work, stats=False)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    k_arn, k_exp, k_cmb = [], [], []
+    for i in range(steps):
+        if flush is not None:
+            flush.fill_(i & 0xFF)           # evict L2 between timed steps
+        ev[i][0].record(stream)
+        _, st = lsa.phiv(op, v, h, p, m, variant=variant, precision=precision, y=y, work=work, stats=True)
+        ev[i][1].record(stream)
+        if st["status"] < 0:
+            raise RuntimeError(f"phiv failed: {st}")
+        k_arn.append(st["ms_arnoldi"])
+        k_exp.append(st["ms_expm"])
+        k_cmb.append(st["ms_combine"])
+    torch.cuda.synchronize()
+    return dict(step_ms=[a.elapsed_time(b) for a, b in ev], k_arn=k_arn, k_exp=k_exp, k_cmb=k_cmb, st0=st0,
+                op=op, v=v, v_host=v_host, y=y, work=work, inp=inp, N=N)
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
@@ -820,55 +895,26 @@ def main():
         return
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    inp = W.make_inputs(cfg)
-    N = W.n_dof(cfg)
     p, m, h = cfg["p"], cfg["m"], cfg["h"]
-    fields = {k: torch.from_numpy(v).to(dev) for k, v in inp.items() if k != "v"}
-    v_host = torch.from_numpy(inp["v"]).pin_memory()
-    v = v_host.to(dev)
-    op = lsa.Operator.from_workload(cfg, fields)
-    work = lsa.Workspace.for_call(op, m, p, args.precision)
-    y = torch.empty((p + 1, N), dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream()
     flush = None if args.no_flush else torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-
-    # first call: status and statistics
-    _, st0 = lsa.phiv(op, v, h, p, m, variant=args.variant, precision=args.precision, y=y, work=work)
-    m_eff = st0["m_eff"]
-    for _ in range(args.warmup):
-        lsa.phiv(op, v, h, p, m, variant=args.variant, precision=args.precision, y=y, work=work,
-                 stats=False)
-    torch.cuda.synchronize()
 
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    k_arn = []
-    k_exp = []
-    k_cmb = []
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    for i in range(args.steps):
-        if flush is not None:
-            flush.fill_(i & 0xFF)           # evict L2 between timed steps
-        ev[i][0].record(stream)
-        _, st = lsa.phiv(op, v, h, p, m, variant=args.variant, precision=args.precision, y=y,
-                         work=work, stats=True)
-        ev[i][1].record(stream)
-        if st["status"] < 0:
-            raise RuntimeError(f"phiv failed: {st}")
-        k_arn.append(st["ms_arnoldi"])
-        k_exp.append(st["ms_expm"])
-        k_cmb.append(st["ms_combine"])
-    torch.cuda.synchronize()
+    R = time_phiv(lsa, torch, cfg, args.precision, args.variant, args.steps, args.warmup, dev, flush, stream)
     if world > 1:
         torch.distributed.barrier()
     clocks = sampler.stop()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    tot_ms = sum(step_ms)
+    # the float64 roofline's denominator: FMA throughput measured on this GPU
+    # (after the timed region, on a warm GPU)
+    fp64_pk, fp64_src = fp64_peak(lsa)
+    op, v, v_host, y, work, N, st0 = R["op"], R["v"], R["v_host"], R["y"], R["work"], R["N"], R["st0"]
+    m_eff = st0["m_eff"]
+    tot_ms = sum(R["step_ms"])
     tot_ms, value = aggregate_replicas(tot_ms, args.steps, world, dev)
 
     # the paper's metric: runtime of the one-reduce method over the incomplete-
@@ -892,45 +938,28 @@ def main():
         lsa.phiv(op, v, h, p, m, variant=args.variant, precision=args.precision, y=y, work=work,
                  stats=False)      # y back to the measured variant's result
 
-    # end-to-end through the public API with host buffers: H2D of v, phiv, D2H of y
+    # end to end through one C-ABI call with host buffers (lsa_phiv_host): the
+    # H2D copy of v, the phi product and the D2H copy of y, every step
     y_host = torch.empty((p + 1, N), dtype=torch.float64).pin_memory()
+    v_dev = torch.empty(N, dtype=torch.float64, device=dev)
+    y_dev = torch.empty((p + 1, N), dtype=torch.float64, device=dev)
     e2e_steps = max(3, min(args.steps, 10))
+    lsa.phiv_host(op, v_host, h, p, m, y_host, v_dev, y_dev, variant=args.variant, precision=args.precision,
+                  work=work)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for i in range(e2e_steps):
-        v_dev = v_host.to(dev, non_blocking=True)
-        lsa.phiv(op, v_dev, h, p, m, variant=args.variant, precision=args.precision, y=y, work=work,
-                 stats=False)
-        y_host.copy_(y, non_blocking=True)
+        lsa.phiv_host(op, v_host, h, p, m, y_host, v_dev, y_dev, variant=args.variant,
+                      precision=args.precision, work=work)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_value = e2e_steps / (e0.elapsed_time(e1) / 1e3) * world
+    e2e_match = bool(torch.equal(y_host, y.cpu()))
 
-    # roofline of the dominant kernel (the persistent Arnoldi kernel)
-    byts, flops = algorithmic_counts(cfg, args.precision, m_eff)
-    ms_a = statistics.mean(k_arn)
-    hbm_peak, peak_kind = load_peaks()
-    if args.precision == "fp64":
-        achieved = flops / (ms_a / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS,
-                "traffic": PROFILED_TRAFFIC.get((cfg["name"], args.precision, args.variant)),
-                "kernel": "k_arnoldi (persistent hybrid Arnoldi)",
-                "peak_source": "FP64 FMA pipe from unit counts and max clock (152 SMs x 2 FMA/clk x 2.07 GHz)",
-                "hbm_gbs": byts / (ms_a / 1e3) / 1e9, "hbm_frac": byts / (ms_a / 1e3) / 1e9 / hbm_peak,
-                "algorithmic_bytes": byts, "algorithmic_flops": flops}
-    else:
-        achieved = byts / (ms_a / 1e3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak,
-                "traffic": PROFILED_TRAFFIC.get((cfg["name"], args.precision, args.variant)),
-                "kernel": {0: "k_arnoldi", 1: "k_arnoldi_tma", 2: "k_arnoldi_stream"}[st0["arnoldi_kernel"]]
-                          + " (persistent Arnoldi, float32 basis)",
-                "peak_source": f"{peak_kind} hbm_gbs",
-                "algorithmic_bytes": byts, "algorithmic_flops": flops}
-
+    ms_a = statistics.mean(R["k_arn"])
+    roof = phiv_roofline(cfg, args.precision, args.variant, ms_a, m_eff, st0["arnoldi_kernel"], fp64_pk, fp64_src)
     line = {"metric": METRIC, "value": value, "unit": "phiv/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -943,8 +972,8 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "arnoldi_steps_per_s": value * m_eff,
             "grid_syncs_per_step": st0["grid_syncs"] / max(m_eff, 1),
-            "kernel_ms": {"arnoldi": ms_a, "expm": statistics.mean(k_exp),
-                          "combine": statistics.mean(k_cmb)},
+            "kernel_ms": {"arnoldi": ms_a, "expm": statistics.mean(R["k_exp"]),
+                          "combine": statistics.mean(R["k_cmb"])},
             "roofline": roof,
             "vs_iocgs": None if io_ms is None else
             {"ms_iocgs": io_ms, "ms_variant": tot_ms / args.steps, "ratio": (tot_ms / args.steps) / io_ms,
@@ -952,15 +981,61 @@ def main():
              "note": "runtime of this variant / incomplete-orthogonalisation ioCGS, the paper's metric; "
                      "the paper's ratios (0.55-1.28) are whole integrator runs on CPU clusters"},
             "e2e": {"value": e2e_value, "unit": "phiv/s", "h2d_bytes_per_step": N * 8,
-                    "d2h_bytes_per_step": (p + 1) * N * 8},
+                    "d2h_bytes_per_step": (p + 1) * N * 8,
+                    "call": "lsa_phiv_host (C ABI, host buffers; copies and phi product on one stream)",
+                    "y_equals_device_result": e2e_match},
             "gpu_launches": 4 * args.steps,
             "clocks": clocks}
+
+    # the 3D float32-basis workload, timed in the default run as a nested block
+    d3 = None
+    if args.config == 1 and not args.size and world == 1 and args.precision == "fp64":
+        cfg3 = workload(2)
+        del R
+        sampler3 = ClockSampler(local)
+        sampler3.start()
+        time.sleep(0.3)
+        steps3 = max(3, min(args.steps, 5))
+        R3 = time_phiv(lsa, torch, cfg3, "fp32", "hcwy", steps3, max(3, min(args.warmup, 3)), dev, flush, stream)
+        clocks3 = sampler3.stop()
+        st3 = R3["st0"]
+        ms3 = statistics.mean(R3["k_arn"])
+        d3 = {"workload": cfg3["name"], "N": R3["N"], "m": cfg3["m"], "p": cfg3["p"], "h": cfg3["h"],
+              "variant": "hcwy", "precision": "fp32 basis, float64 Hessenberg and small exponential",
+              "steps": steps3, "phiv_per_s": steps3 / (sum(R3["step_ms"]) / 1e3),
+              "ms_per_step": sum(R3["step_ms"]) / steps3,
+              "arnoldi_steps_per_s": st3["m_eff"] / (ms3 / 1e3),
+              "grid_syncs_per_step": st3["grid_syncs"] / max(st3["m_eff"], 1),
+              "kernel_ms": {"arnoldi": ms3, "expm": statistics.mean(R3["k_exp"]),
+                            "combine": statistics.mean(R3["k_cmb"])},
+              "roofline": phiv_roofline(cfg3, "fp32", "hcwy", ms3, st3["m_eff"], st3["arnoldi_kernel"],
+                                        fp64_pk, fp64_src),
+              "clocks": clocks3}
+        y3 = R3["y"].cpu().numpy()
+        del R3
+        line["adr3d_256_fp32"] = d3
     if rank == 0 and world == 1 and not args.no_cpu:
         cb, y_ref = cpu_baseline(cfg, "mgs", args.cpu_budget)
         line["cpu_baseline"] = cb
         yc = y.cpu().numpy()
         line["rel_err_vs_oracle"] = max(float(np.linalg.norm(yc[k] - y_ref[k]) / np.linalg.norm(y_ref[k]))
                                         for k in range(p + 1))
+        line["max_abs_err_vs_oracle"] = max(float(np.max(np.abs(yc[k] - y_ref[k])) / np.max(np.abs(y_ref[k])))
+                                            for k in range(p + 1))
+        if d3 is not None:
+            # the oracle's H-CWY form (pinned equal to its MGS) on the full 256^3 grid
+            from oracle import krylov as OK
+            from oracle import operators as OP
+
+            inp3 = W.make_inputs(cfg3)
+            A3 = OP.from_workload(cfg3, inp3)
+            t0 = time.perf_counter()
+            r3, _ = OK.phiv(lambda x: A3 @ x, inp3["v"], cfg3["h"], cfg3["p"], cfg3["m"], "hcwy")
+            d3["rel_err_vs_oracle"] = max(float(np.linalg.norm(y3[k] - r3[k]) / np.linalg.norm(r3[k]))
+                                          for k in range(cfg3["p"] + 1))
+            d3["max_abs_err_vs_oracle"] = max(float(np.max(np.abs(y3[k] - r3[k])) / np.max(np.abs(r3[k])))
+                                              for k in range(cfg3["p"] + 1))
+            d3["oracle_s"] = time.perf_counter() - t0
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -259,6 +259,27 @@ lsa_status lsa_phiv_lincomb_adaptive_m(const lsa_op* op, const double* b, int p,
                                        size_t work_bytes, lsa_stats* stats, int* substeps, int* rejected,
                                        int* dims, int dims_cap, void* stream);
 
+/* lsa_phiv from and to host memory, for callers whose vectors live on the host:
+ * copies v (v_host -> v_dev), runs lsa_phiv into y_dev, copies y back
+ * (y_dev -> y_host), all enqueued on `stream` in that order; the call returns
+ * once they are enqueued (synchronise the stream before reading y_host).
+ *  v_host     host, N doubles (pinned memory lets the copy overlap).
+ *  y_host     host, (p+1) x N doubles, row k = phi_k(hA)v.
+ *  v_dev      dev, N doubles;  y_dev  dev, (p+1) x N doubles (caller-owned
+ *             staging buffers, distinct).
+ *  Other arguments as lsa_phiv (no stats).  Returns lsa_phiv's status, or
+ *  LSA_ERR_CUDA when a copy cannot be enqueued. */
+lsa_status lsa_phiv_host(const lsa_op* op, const double* v_host, double h, int p, int m, double tol,
+                         int variant, int precision, double* y_host, double* v_dev, double* y_dev,
+                         void* work, size_t work_bytes, void* stream);
+
+/* Measurement utility (not part of the paper's method): a kernel of
+ * independent float64 fused multiply-add chains on every SM, `iters` FMAs per
+ * chain, for the float64 roofline's denominator.  out: dev, 1 double (a
+ * checksum that keeps the chains live).  Returns the FLOPs it executes (2 per
+ * FMA) in *flops; time it with events on `stream`. */
+lsa_status lsa_probe_fp64_fma(int iters, double* out, double* flops, void* stream);
+
 /* Exponential-integrator building blocks (Sect. 4) besides the phi products.
  * lsa_rhs: f = F(u) for the Gray-Scott system whose Jacobian at a state is
  *   the LSA_OP_GRAYSCOTT2D operator: F(u, v) = [Du Lap u - u v^2 + F (1 - u);

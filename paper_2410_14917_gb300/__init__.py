@@ -188,6 +188,48 @@ def phiv(op: Operator, v: torch.Tensor, h: float, p: int, m: int, tol: float = 0
     return y, (s.as_dict() if stats else None)
 
 
+def phiv_host(op: Operator, v_host: torch.Tensor, h: float, p: int, m: int, y_host: torch.Tensor,
+              v_dev: torch.Tensor, y_dev: torch.Tensor, tol: float = 0.0, variant="hcwy", precision="fp64",
+              work=None, stream=None):
+    """phiv from and to host memory (lsa_phiv_host): v_host (N,) and y_host (p+1, N)
+    float64 CPU tensors (pinned for overlap), v_dev and y_dev device staging
+    tensors of the same shapes.  Enqueues H2D, the phi product and D2H on the
+    stream; returns the status (synchronise before reading y_host)."""
+    for t_, name, dev in ((v_host, "v_host", False), (y_host, "y_host", False), (v_dev, "v_dev", True),
+                          (y_dev, "y_dev", True)):
+        if t_.dtype != torch.float64 or not t_.is_contiguous() or t_.is_cuda != dev:
+            raise ValueError(f"{name} must be a contiguous float64 {'CUDA' if dev else 'CPU'} tensor")
+    N = v_host.numel()
+    if v_dev.numel() != N or y_host.numel() != (p + 1) * N or y_dev.numel() != (p + 1) * N:
+        raise ValueError("v and y buffers must hold N and (p+1) N values")
+    work = work or Workspace.for_call(op, min(m, N), p, precision)
+    st = B.lib().lsa_phiv_host(ctypes.byref(op.c), ctypes.c_void_p(v_host.data_ptr()), float(h), int(p), int(m),
+                               float(tol), VARIANTS[variant], PRECISIONS[precision],
+                               ctypes.c_void_p(y_host.data_ptr()), _ptr(v_dev), _ptr(y_dev),
+                               ctypes.c_void_p(work.ptr), work.nbytes, _stream_ptr(stream))
+    return _check(st, "lsa_phiv_host")
+
+
+def probe_fp64_fma_tflops(iters: int = 20000, reps: int = 10, device="cuda"):
+    """Measured float64 FMA throughput (TFLOP/s, best of reps) of
+    lsa_probe_fp64_fma, timed with CUDA events on the current stream."""
+    out = torch.zeros(1, dtype=torch.float64, device=device)
+    flops = ctypes.c_double(0.0)
+    stream = torch.cuda.current_stream()
+    best = 0.0
+    for r in range(reps + 1):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _check(B.lib().lsa_probe_fp64_fma(int(iters), _ptr(out), ctypes.byref(flops), _stream_ptr(None)),
+               "lsa_probe_fp64_fma", ok=(B.LSA_OK,))
+        b.record(stream)
+        b.synchronize()
+        if r > 0:                      # the first launch is a warm-up
+            best = max(best, flops.value / (a.elapsed_time(b) / 1e3) / 1e12)
+    return best
+
+
 def phiv_lincomb(op: Operator, b: torch.Tensor, tau: float, m: int, nsub: int = 1, tol: float = 0.0,
                  variant="hcwy", u=None, work=None, stream=None, stats=True):
     """u = sum_j tau^j phi_j(tau A) b[j] (b: (p+1, N) float64 CUDA tensor) by Krylov

@@ -63,6 +63,9 @@ SIGNATURES = {
                                             c_int, c_int, c_int, c_int, c_int, c_void_p, c_void_p,
                                             c_void_p, c_size_t, POINTER(LsaStats), POINTER(c_int),
                                             POINTER(c_int), POINTER(c_int), c_int, c_void_p]),
+    "lsa_phiv_host": (c_int, [POINTER(LsaOp), c_void_p, c_double, c_int, c_int, c_double, c_int, c_int,
+                              c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "lsa_probe_fp64_fma": (c_int, [c_int, c_void_p, POINTER(c_double), c_void_p]),
     "lsa_rhs": (c_int, [POINTER(LsaOp), c_void_p, c_void_p, c_void_p]),
     "lsa_axpby": (c_int, [c_longlong, c_double, c_void_p, c_double, c_void_p, c_void_p, c_void_p]),
     "lsa_expm_phi": (c_int, [c_void_p, c_int, c_int, c_double, c_int, c_void_p, c_void_p, c_size_t,

@@ -490,6 +490,23 @@ lsa_status lsa_phiv(const lsa_op* op, const double* v, double h, int p, int m, d
   return LSA_OK;
 }
 
+lsa_status lsa_phiv_host(const lsa_op* op, const double* v_host, double h, int p, int m, double tol,
+                         int variant, int precision, double* y_host, double* v_dev, double* y_dev,
+                         void* work, size_t work_bytes, void* stream) {
+  if (!v_host || !y_host || !v_dev || !y_dev) return LSA_ERR_ARG;
+  const long long N = lsa_op_dof(op);
+  if (N < 1 || p < 0 || p > PMAX) return LSA_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(v_dev, v_host, (size_t)N * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return LSA_ERR_CUDA;
+  lsa_status st = lsa_phiv(op, v_dev, h, p, m, tol, variant, precision, y_dev, work, work_bytes, nullptr, stream);
+  if (st < 0) return st;
+  if (cudaMemcpyAsync(y_host, y_dev, (size_t)(p + 1) * N * sizeof(double), cudaMemcpyDeviceToHost, s) !=
+      cudaSuccess)
+    return LSA_ERR_CUDA;
+  return st;
+}
+
 lsa_status lsa_phiv_lincomb(const lsa_op* op, const double* b, int p, double tau, int nsub, int m,
                             double tol, int variant, int precision, double* u, void* work,
                             size_t work_bytes, lsa_stats* stats, void* stream) {
