@@ -26,6 +26,8 @@ cudaError_t launch_arnoldi_tma_adr3d(const ArnoldiParams&, int, int, cudaStream_
 bool stream_applicable_advdiff2d(const DevOp&, const Tiling&, int);
 bool stream_applicable_adr3d(const DevOp&, const Tiling&, int);
 cudaError_t launch_arnoldi_stream_advdiff2d(const ArnoldiParams&, cudaStream_t);
+bool cluster_applicable_advdiff2d(const DevOp&, const Tiling&, int);
+cudaError_t launch_arnoldi_cluster_advdiff2d(const ArnoldiParams&, const SmallParams*, double*, cudaStream_t);
 cudaError_t launch_arnoldi_stream_adr3d(const ArnoldiParams&, cudaStream_t);
 
 cudaError_t launch_arnoldi_grayscott2d_t(const ArnoldiParams&, int, int, cudaStream_t);
@@ -177,11 +179,30 @@ static bool use_stream(const ArnoldiParams& P, int precision) {
   return false;
 }
 
+// The single-cluster kernel (basis in the CTAs' shared memory, cluster
+// barriers) runs the hybrid variants in float64 on small 2D advection-diffusion
+// grids (at most 16 tiles of 16 x 16) when the device can place such a cluster
+// (LSA_CLUSTER=0 in the environment disables it).  The device check is cached
+// per device and m.
+static bool use_cluster(const ArnoldiParams& P, int precision) {
+  if (!is_hybrid(P.variant) || precision != LSA_FP64 || P.naug > 0 || P.op.kind != LSA_OP_ADVDIFF2D) return false;
+  if (P.op.nx % TX != 0 || P.op.ny % TY != 0 || P.tl.tiles_x * P.tl.tiles_y > 16) return false;
+  const char* env = getenv("LSA_CLUSTER");
+  if (env && env[0] == '0') return false;
+  static signed char cache[64][MMAX + 1][17];   // 0 unknown, 1 yes, -1 no
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || P.m < 1 || P.m > MMAX) return false;
+  signed char& c = cache[dev][P.m][P.tl.tiles_x * P.tl.tiles_y];
+  if (c == 0) c = cluster_applicable_advdiff2d(P.op, P.tl, P.m) ? 1 : -1;
+  return c > 0;
+}
+
 static int arnoldi_kernel_kind(const ArnoldiParams& P, int precision) {
-  return use_stream(P, precision) ? 2 : use_tma(P, precision) ? 1 : 0;
+  return use_cluster(P, precision) ? 3 : use_stream(P, precision) ? 2 : use_tma(P, precision) ? 1 : 0;
 }
 
 cudaError_t launch_arnoldi(const ArnoldiParams& P, int precision, int G, cudaStream_t s) {
+  if (use_cluster(P, precision)) return launch_arnoldi_cluster_advdiff2d(P, nullptr, nullptr, s);
   if (use_stream(P, precision)) {
     if (P.op.kind == LSA_OP_ADVDIFF2D) return launch_arnoldi_stream_advdiff2d(P, s);
     return launch_arnoldi_stream_adr3d(P, s);
@@ -453,28 +474,34 @@ lsa_status lsa_phiv(const lsa_op* op, const double* v, double h, int p, int m, d
   cudaError_t e = launch_init(P.ctl, pr.d, (float*)pr.d.g0, (float*)pr.d.g1, precision, P.H,
                               (m + 1) * m, v, P.V, s, use_stream(P, precision) ? P.E : nullptr);
   tm.mark(0);
-  if (e == cudaSuccess) e = launch_arnoldi(P, precision, pr.L.G, s);
-  tm.mark(1);
-  if (e == cudaSuccess) {
-    SmallParams S;
-    memset(&S, 0, sizeof(S));
-    S.H = P.H;
-    S.ldh = m + 1;
-    S.ctl_in = P.ctl;
-    S.ctl = P.ctl;
-    S.m = m;
-    S.p = p;
-    S.h = h;
-    S.mats = (double*)(pr.w + pr.L.small);
-    S.C = (double*)(pr.w + pr.L.coefs);
-    S.ldc = MMAX + 2;
-    S.scale_out = 1;
-    S.timeout_ns = kTimeoutNs;
-    S.tol = tol;
-    e = launch_expm(S, s);
+  SmallParams S;
+  memset(&S, 0, sizeof(S));
+  S.H = P.H;
+  S.ldh = m + 1;
+  S.ctl_in = P.ctl;
+  S.ctl = P.ctl;
+  S.m = m;
+  S.p = p;
+  S.h = h;
+  S.mats = (double*)(pr.w + pr.L.small);
+  S.C = (double*)(pr.w + pr.L.coefs);
+  S.ldc = MMAX + 2;
+  S.scale_out = 1;
+  S.timeout_ns = kTimeoutNs;
+  S.tol = tol;
+  // the single-cluster kernel runs S1-S6 in one launch
+  const bool fused = use_cluster(P, precision);
+  if (fused) {
+    if (e == cudaSuccess) e = launch_arnoldi_cluster_advdiff2d(P, &S, y, s);
+    tm.mark(1);
     tm.mark(2);
-    if (e == cudaSuccess)
-      e = launch_combine(P.V, precision, N, S.C, S.ldc, p, P.ctl, y, s);
+    tm.mark(3);
+  } else {
+    if (e == cudaSuccess) e = launch_arnoldi(P, precision, pr.L.G, s);
+    tm.mark(1);
+    if (e == cudaSuccess) e = launch_expm(S, s);
+    tm.mark(2);
+    if (e == cudaSuccess) e = launch_combine(P.V, precision, N, S.C, S.ldc, p, P.ctl, y, s);
     tm.mark(3);
   }
   if (e != cudaSuccess) return LSA_ERR_CUDA;
@@ -483,7 +510,7 @@ lsa_status lsa_phiv(const lsa_op* op, const double* v, double h, int p, int m, d
     stats->ms_arnoldi = tm.ms(0, 1);
     stats->ms_expm = tm.ms(1, 2);
     stats->ms_combine = tm.ms(2, 3);
-    stats->launches = 4;
+    stats->launches = fused ? 2 : 4;
     stats->arnoldi_kernel = arnoldi_kernel_kind(P, precision);
     return r;
   }

@@ -1,6 +1,7 @@
 // Arnoldi kernels instantiated for the advdiff2d operator (one translation unit
 // per operator so that the library builds in parallel).
 #include "lsa_batched.cuh"
+#include "lsa_cluster.cuh"
 #include "lsa_stream.cuh"
 #include "lsa_tma.cuh"
 
@@ -28,6 +29,14 @@ bool stream_applicable_advdiff2d(const DevOp& d, const Tiling& tl, int m) {
 }
 cudaError_t launch_arnoldi_stream_advdiff2d(const ArnoldiParams& P, cudaStream_t s) {
   return launch_arnoldi_stream_op<OpAdvDiff2D>(P, s);
+}
+
+bool cluster_applicable_advdiff2d(const DevOp& d, const Tiling& tl, int m) {
+  return cluster_applicable_op<OpAdvDiff2D>(d, tl, m);
+}
+cudaError_t launch_arnoldi_cluster_advdiff2d(const ArnoldiParams& P, const SmallParams* SP, double* y,
+                                             cudaStream_t s) {
+  return launch_arnoldi_cluster_op<OpAdvDiff2D>(P, SP, y, s);
 }
 
 cudaError_t launch_batched_advdiff2d(const BatchParams& BP, int precision, int G, cudaStream_t s) {

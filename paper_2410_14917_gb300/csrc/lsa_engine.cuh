@@ -60,11 +60,23 @@ struct Engine {
     int aug_xcol, aug_wcol;          // ... and the columns they belong to (-1: not stored)
     Tc a;
     int flag, done, fallback_pending, stop;
+    // cached mode (one CTA runs every step): lazy scales, norm estimate and
+    // ||A v_j|| of the last step, kept here instead of re-read from global
+    double sig[MMAX + 2];
+    double nrm_est_c, aw_prev_c;
+    int syncs_c;                     // reductions counted so far (cached mode)
   };
 
   const ArnoldiParams& P;
   Smem& S;
   double* small;                     // MMAX x MMAX scratch of the last-arriving CTA
+  // Cached mode: the same CTA runs every step (the single-cluster kernel), so T
+  // (and GSMGS's L, in smallL) stay in shared memory between steps, the lazy
+  // scales and scalars are read from S, and the step also leaves the next
+  // pass's coefficients and flags in S (S.coefc, S.a, S.done,
+  // S.fallback_pending).  Global copies are written as in the grid kernels.
+  bool cached = false;
+  double* smallL = nullptr;
   Coef<Tc> cf;
   const int tid, lane, warp;
   int grank, gsize;                  // this CTA's rank in its group and the group size
@@ -617,9 +629,11 @@ struct Engine {
         if (j == 1) {
           ctl->beta = sqrt(Gj);
         } else {
-          double tn = __ldcg(&ctl->nrm_est) * sqrt(Gj);   // true norm of the previous vector
+          const double ne_prev = cached ? S.nrm_est_c : __ldcg(&ctl->nrm_est);
+          const double aw_prev = cached ? S.aw_prev_c : __ldcg(&ctl->aw_prev);
+          double tn = ne_prev * sqrt(Gj);                  // true norm of the previous vector
           S.true_nrm = tn;
-          if (!(tn > P.brk_tol * __ldcg(&ctl->aw_prev))) { // lagged breakdown test
+          if (!(tn > P.brk_tol * aw_prev)) {               // lagged breakdown test
             Hat(j - 1, j - 2) = tn;
             ctl->m_eff = j - 1;
             ctl->breakdown = 1;
@@ -628,15 +642,17 @@ struct Engine {
           }
         }
         ctl->sigma[j - 1] = sj;
+        S.sig[j - 1] = sj;
         temp2[np] = sj * sj * Pj;
         temp2[np + 1] = sj * sj * Q;
       }
-      ctl->syncs = __ldcg(&ctl->syncs) + 1;
+      ctl->syncs = cached ? ++S.syncs_c : __ldcg(&ctl->syncs) + 1;
+      if (cached && S.flag) S.done = 1;
     }
     __syncthreads();
     if (S.flag) return;
     for (int i = tid; i < np; i += NT) {
-      double si = __ldcg(&ctl->sigma[i]);
+      double si = cached ? S.sig[i] : __ldcg(&ctl->sigma[i]);
       temp1[i] = si * S.sj * S.red[i];
       temp2[i] = si * S.sj * S.red[np + i];
     }
@@ -646,7 +662,7 @@ struct Engine {
     } else {
       // New row of T (Alg. 5: T_{j,1:j-1} = -temp_{1:j-1,1}^T T_{1:j-1,1:j-1};
       // Alg. 6: T_{j,1:j-1} = -temp_{1:j-1,1}^T; for Alg. 7 this is M^{-1}).
-      stage(P.T, np);
+      if (!cached) stage(P.T, np);   // cached: small already holds rows 0..np-1 of T
       for (int k = tid; k < np; k += NT) {
         double acc = -temp1[k];
         if (P.variant != LSA_HNCWY) {
@@ -672,22 +688,23 @@ struct Engine {
         // Alg. 7: y = M^{-1} temp2; p = (I + N M^{-1}) temp2 = temp2 - L^T y;
         // H_{1:j,j} solves (I + L) x = p.
         apply_unit_lower(temp2, aux, j);                  // aux = y
-        stage(P.L, np);
+        double* Lm = cached ? smallL : small;             // L (cached: kept between steps)
+        if (!cached) stage(P.L, np);
         for (int k = tid; k < np; k += NT) {
-          small[np * MMAX + k] = temp1[k];
+          Lm[np * MMAX + k] = temp1[k];
           P.L[np * MMAX + k] = temp1[k];
         }
         __syncthreads();
         for (int r = tid; r < j; r += NT) {
           double acc = 0.0;
-          for (int k = r + 1; k < j; ++k) acc = fma(small[k * MMAX + r], aux[k], acc);
+          for (int k = r + 1; k < j; ++k) acc = fma(Lm[k * MMAX + r], aux[k], acc);
           hcol[r] = temp2[r] - acc;
         }
         __syncthreads();
         if (warp == 0) {                                   // forward substitution
           for (int r = 0; r < j; ++r) {
             double acc = 0.0;
-            for (int k = lane; k < r; k += 32) acc = fma(small[r * MMAX + k], hcol[k], acc);
+            for (int k = lane; k < r; k += 32) acc = fma(Lm[r * MMAX + k], hcol[k], acc);
             acc = warp_sum(acc);
             if (lane == 0) hcol[r] = hcol[r] - acc;
             __syncwarp();
@@ -709,10 +726,13 @@ struct Engine {
       double t = temp2[j];
       double awn = sqrt(t);
       S.scale = 1.0;
+      bool done_now = false;
       if (t < S.ss) {                         // Pythagorean radicand negative: explicit norm
         ctl->fallbacks = __ldcg(&ctl->fallbacks) + 1;
         ctl->fallback_pending = 1;
         ctl->nrm_est = 1.0;
+        S.nrm_est_c = 1.0;
+        if (cached) S.fallback_pending = 1;
       } else {
         double ne = sqrt(t - S.ss);           // Eq. 18
         if (!(ne > P.brk_tol * awn)) {
@@ -720,18 +740,27 @@ struct Engine {
           ctl->m_eff = j;
           ctl->breakdown = 1;
           ctl->done = 1;
+          done_now = true;
         }
         ctl->nrm_est = ne;
+        S.nrm_est_c = ne;
         S.scale = (ne > 0.0) ? 1.0 / ne : 0.0;
       }
       ctl->aw_prev = awn;
+      S.aw_prev_c = awn;
       ctl->a = S.sj * S.scale;
-      if (j == P.m && !__ldcg(&ctl->done)) ctl->m_eff = P.m;
+      if (cached) {
+        S.a = (Tc)(S.sj * S.scale);
+        if (done_now) S.done = 1;
+      }
+      if (j == P.m && !done_now && !__ldcg(&ctl->done)) ctl->m_eff = P.m;
     }
     __syncthreads();
     for (int i = tid; i < j; i += NT) {
-      double si = (i == j - 1) ? S.sj : __ldcg(&ctl->sigma[i]);
-      ctl->coef[i] = si * hcol[i] * S.scale;
+      double si = (i == j - 1) ? S.sj : (cached ? S.sig[i] : __ldcg(&ctl->sigma[i]));
+      const double c = si * hcol[i] * S.scale;
+      ctl->coef[i] = c;
+      if (cached) S.coefc[i] = (Tc)c;
     }
   }
 
@@ -774,20 +803,27 @@ struct Engine {
     Ctl* ctl = P.ctl;
     if (tid == 0) {
       double nrm = sqrt(S.red[0]);
-      ctl->syncs = __ldcg(&ctl->syncs) + 1;
-      if (!(nrm > P.brk_tol * __ldcg(&ctl->aw_prev))) {
+      ctl->syncs = cached ? ++S.syncs_c : __ldcg(&ctl->syncs) + 1;
+      if (!(nrm > P.brk_tol * (cached ? S.aw_prev_c : __ldcg(&ctl->aw_prev)))) {
         Hat(j, j - 1) = nrm;
         ctl->m_eff = j;
         ctl->breakdown = 1;
         ctl->done = 1;
+        if (cached) S.done = 1;
       }
       ctl->nrm_est = nrm;
+      S.nrm_est_c = nrm;
       S.scale = (nrm > 0.0) ? 1.0 / nrm : 0.0;
-      ctl->a = __ldcg(&ctl->a) * S.scale;
+      ctl->a = (cached ? (double)S.a : __ldcg(&ctl->a)) * S.scale;
       ctl->fallback_pending = 0;
+      if (cached) { S.a = (Tc)(S.a * S.scale); S.fallback_pending = 0; }
     }
     __syncthreads();
-    for (int i = tid; i < j; i += NT) ctl->coef[i] = __ldcg(&ctl->coef[i]) * S.scale;
+    for (int i = tid; i < j; i += NT) {
+      const double c = (cached ? (double)S.coefc[i] : __ldcg(&ctl->coef[i])) * S.scale;
+      ctl->coef[i] = c;
+      if (cached) S.coefc[i] = (Tc)c;
+    }
   }
 
   __device__ void hybrid_final_finish() {
@@ -795,12 +831,12 @@ struct Engine {
     if (tid == 0) {
       const int m = P.m;
       double nrm = sqrt(S.red[0]);
-      double hl = __ldcg(&ctl->nrm_est) * nrm;       // true norm of the projected v_{m+1}
+      double hl = (cached ? S.nrm_est_c : __ldcg(&ctl->nrm_est)) * nrm;   // true norm of the projected v_{m+1}
       Hat(m, m - 1) = hl;
       ctl->h_last = hl;
       ctl->sigma[m] = (nrm > 0.0) ? 1.0 / nrm : 0.0;
-      ctl->syncs = __ldcg(&ctl->syncs) + 1;
-      if (!(hl > P.brk_tol * __ldcg(&ctl->aw_prev))) ctl->breakdown = 1;
+      ctl->syncs = cached ? ++S.syncs_c : __ldcg(&ctl->syncs) + 1;
+      if (!(hl > P.brk_tol * (cached ? S.aw_prev_c : __ldcg(&ctl->aw_prev)))) ctl->breakdown = 1;
     }
   }
 
@@ -944,7 +980,7 @@ struct Engine {
       Ctl* ctl = P.ctl;
       double nrm = sqrt(S.red[0]);
       Hat(j, j - 1) = nrm;
-      ctl->syncs = __ldcg(&ctl->syncs) + 1;
+      ctl->syncs = cached ? ++S.syncs_c : __ldcg(&ctl->syncs) + 1;
       if (!(nrm > P.brk_tol * __ldcg(&ctl->aw_prev))) {
         ctl->m_eff = j;
         ctl->breakdown = 1;

@@ -54,8 +54,12 @@ __device__ __forceinline__ double block_coef(const double* X, const double* X2, 
 }
 
 // The exponential, run by a group of gsize CTAs (grank = this CTA's rank):
-// the whole grid for the standalone kernel, a slice of it in the batched one.
-// Ends with a group barrier, so its coefficients are visible to the group.
+// the whole grid for the standalone kernel, a slice of it in the batched one,
+// the CTAs of one cluster in the single-cluster kernel (kCluster: the group
+// barriers are then the hardware cluster barrier instead of the bounded
+// global-memory one).  Ends with a group barrier, so its coefficients are
+// visible to the group.
+template <bool kCluster = false>
 static __device__ __noinline__ bool expm_group(const SmallParams& P, int grank, int gsize, ExpmShared& sh) {
   Ctl* ctl = P.ctl;
   const BarrierRef br = expm_barrier(ctl);
@@ -84,6 +88,11 @@ static __device__ __noinline__ bool expm_group(const SmallParams& P, int grank, 
 
   // the closing group barrier of the early exits (generation 0: no product ran)
   auto close0 = [&]() -> bool {
+    if constexpr (kCluster) {
+      __syncthreads();
+      cluster_barrier();
+      return true;
+    }
     int r = barrier_arrive(br, 0u, G, &sh.flag, P.timeout_ns);
     if (r < 0) return false;
     if (r == 1) barrier_release(br, 0u);
@@ -133,9 +142,14 @@ static __device__ __noinline__ bool expm_group(const SmallParams& P, int grank, 
 
 #define EXPM_BARRIER()                                                          \
   do {                                                                          \
-    int _r = barrier_arrive(br, gen, G, &sh.flag, P.timeout_ns);                \
-    if (_r < 0) return false;                                                   \
-    if (_r == 1) barrier_release(br, gen);                                      \
+    if constexpr (kCluster) {                                                   \
+      __syncthreads();                                                          \
+      cluster_barrier();                                                        \
+    } else {                                                                    \
+      int _r = barrier_arrive(br, gen, G, &sh.flag, P.timeout_ns);              \
+      if (_r < 0) return false;                                                 \
+      if (_r == 1) barrier_release(br, gen);                                    \
+    }                                                                           \
     ++gen;                                                                      \
   } while (0)
 
@@ -207,7 +221,6 @@ static __device__ __noinline__ bool expm_group(const SmallParams& P, int grank, 
     EXPM_BARRIER();
     double* t = Rin; Rin = Rout; Rout = t;
   }
-#undef EXPM_BARRIER
   // extract: C[k][i] = E[i][col_k], col_0 = 0, col_k = m + k - 1 (k = 1..p+1)
   const double beta = P.ctl_in ? __ldcg(&P.ctl_in->beta) : 1.0;
   for (int o = gtid; o < (p + 2) * P.ldc; o += gstride) {
@@ -230,14 +243,10 @@ static __device__ __noinline__ bool expm_group(const SmallParams& P, int grank, 
     ctl->err_est = err;
     if (P.tol > 0.0 && err > P.tol * beta) atomicCAS(&ctl->status, 0, (int)LSA_NOT_CONVERGED);
   }
-  {
-    int r = barrier_arrive(br, gen, G, &sh.flag, P.timeout_ns);
-    if (r < 0) return false;
-    if (r == 1) barrier_release(br, gen);
-    ++gen;
-  }
+  EXPM_BARRIER();
   return true;
 }
+#undef EXPM_BARRIER
 
 
 // Run by a group of gsize CTAs (grank = this CTA's rank).  C and V are read

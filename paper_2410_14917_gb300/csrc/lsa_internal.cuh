@@ -263,6 +263,12 @@ __device__ __forceinline__ void barrier_release(const BarrierRef& b, unsigned ge
   if (threadIdx.x == 0) st_release_u32(b.release, gen + 1u);
 }
 
+// Barrier of all threads of a thread-block cluster: shared and global writes
+// before it are visible to the cluster's threads after it.
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ BarrierRef arnoldi_barrier(Ctl* c) {
   return BarrierRef{&c->arrive, &c->release, &c->abort_flag, &c->status};
 }
