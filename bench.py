@@ -45,10 +45,10 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) of one launch of the dominant kernel from an ncu
 # capture of the current kernel (profiles/k_arnoldi_grayscott2d_512_fp64.md);
 # a workload without an up-to-date capture reports null.
-# The 3D line's capture is of the 160^3 case, scaled by the unknowns (4.096x)
-# (profiles/k_arnoldi_stream_adr3d_160_fp32.md).
-PROFILED_TRAFFIC = {("grayscott2d_512", "fp64", "hcwy"): 9.090663e9 + 0.768122e9,
-                    ("adr3d_256", "fp32", "hcwy"): (16.764652e9 + 1.468302e9) * (256 / 160) ** 3}
+# The 3D line's capture is of the 192^3 case (same tiling), scaled by the
+# unknowns ((256/192)^3) (profiles/k_arnoldi_stream_adr3d_192_fp32.md).
+PROFILED_TRAFFIC = {("grayscott2d_512", "fp64", "hcwy"): 9.153919e9 + 0.772541e9,
+                    ("adr3d_256", "fp32", "hcwy"): (28.721272e9 + 2.551803e9) * (256 / 192) ** 3}
 
 
 def parse():

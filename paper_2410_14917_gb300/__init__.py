@@ -210,7 +210,7 @@ def phiv_host(op: Operator, v_host: torch.Tensor, h: float, p: int, m: int, y_ho
     return _check(st, "lsa_phiv_host")
 
 
-def probe_fp64_fma_tflops(iters: int = 20000, reps: int = 10, device="cuda"):
+def probe_fp64_fma_tflops(iters: int = 2000, reps: int = 10, device="cuda"):
     """Measured float64 FMA throughput (TFLOP/s, best of reps) of
     lsa_probe_fp64_fma, timed with CUDA events on the current stream."""
     out = torch.zeros(1, dtype=torch.float64, device=device)
