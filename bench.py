@@ -43,12 +43,10 @@ FALLBACK_HBM_GBS = 6800.0
 # FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (recipe's unit counts and clock)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) of one launch of the dominant kernel from an ncu
-# capture of the current kernel (profiles/k_arnoldi_grayscott2d_512_fp64.md);
+# capture of the current kernel, keyed by workload, precision, variant and
+# Arnoldi kernel kind (0 one-pass, 4 two-phase grid kernel, 2 streaming);
 # a workload without an up-to-date capture reports null.
-# The 3D line's capture is of the 192^3 case (same tiling), scaled by the
-# unknowns ((256/192)^3) (profiles/k_arnoldi_stream_adr3d_192_fp32.md).
-PROFILED_TRAFFIC = {("grayscott2d_512", "fp64", "hcwy"): 9.153919e9 + 0.772541e9,
-                    ("adr3d_256", "fp32", "hcwy"): (28.721272e9 + 2.551803e9) * (256 / 192) ** 3}
+PROFILED_TRAFFIC = {}
 
 
 def parse():
@@ -818,18 +816,20 @@ def phiv_roofline(cfg, precision, variant, ms_a, m_eff, kernel_kind, fp64_peak, 
         achieved = flops / (ms_a / 1e3) / 1e12
         return {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp64_peak,
-                "traffic": PROFILED_TRAFFIC.get((cfg["name"], precision, variant)),
+                "traffic": PROFILED_TRAFFIC.get((cfg["name"], precision, variant, kernel_kind)),
                 "kernel": ("k_arnoldi_cluster (single thread-block cluster; the time also covers the small "
                            "exponential and the output combination fused into the launch)"
-                           if kernel_kind == 3 else "k_arnoldi (persistent hybrid Arnoldi)"),
+                           if kernel_kind == 3 else
+                           "k_arnoldi (persistent hybrid Arnoldi, two-phase step)" if kernel_kind == 4 else
+                           "k_arnoldi (persistent hybrid Arnoldi, one-pass step)"),
                 "peak_source": fp64_peak_src,
                 "hbm_gbs": byts / (ms_a / 1e3) / 1e9, "hbm_frac": byts / (ms_a / 1e3) / 1e9 / hbm_peak,
                 "algorithmic_bytes": byts, "algorithmic_flops": flops}
     achieved = byts / (ms_a / 1e3) / 1e9
     return {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
             "frac": achieved / hbm_peak,
-            "traffic": PROFILED_TRAFFIC.get((cfg["name"], precision, variant)),
-            "kernel": {0: "k_arnoldi", 1: "k_arnoldi_tma", 2: "k_arnoldi_stream"}[kernel_kind]
+            "traffic": PROFILED_TRAFFIC.get((cfg["name"], precision, variant, kernel_kind)),
+            "kernel": {0: "k_arnoldi", 1: "k_arnoldi_tma", 2: "k_arnoldi_stream", 4: "k_arnoldi"}[kernel_kind]
                       + " (persistent Arnoldi, float32 basis)",
             "peak_source": f"{peak_kind} hbm_gbs",
             "algorithmic_bytes": byts, "algorithmic_flops": flops}
@@ -851,6 +851,9 @@ def time_phiv(lsa, torch, cfg, precision, variant, steps, warmup, dev, flush, st
     op = lsa.Operator.from_workload(cfg, fields)
     work = lsa.Workspace.for_call(op, m, p, precision)
     y = torch.empty((p + 1, N), dtype=torch.float64, device=dev)
+    # the library's step-form tuner (one-pass vs two-phase hybrid step of the
+    # grid kernel; a no-op for the other kernels), before anything is timed
+    two, ms_one, ms_two = lsa.tune_step(op, v, m, variant=variant, precision=precision, reps=3, work=work)
     _, st0 = lsa.phiv(op, v, h, p, m, variant=variant, precision=precision, y=y, work=work)
     for _ in range(warmup):
         lsa.phiv(op, v, h, p, m, variant=variant, precision=precision, y=y, work=work, stats=False)
@@ -871,8 +874,13 @@ def time_phiv(lsa, torch, cfg, precision, variant, steps, warmup, dev, flush, st
         k_cmb.append(st["ms_combine"])
         launches += st["launches"]
     torch.cuda.synchronize()
+    step_form = None
+    if ms_one > 0:
+        step_form = {"chosen": "two-phase" if two else "one-pass", "tuner_ms_one_pass": ms_one,
+                     "tuner_ms_two_phase": ms_two}
     return dict(step_ms=[a.elapsed_time(b) for a, b in ev], k_arn=k_arn, k_exp=k_exp, k_cmb=k_cmb, st0=st0,
-                op=op, v=v, v_host=v_host, y=y, work=work, inp=inp, N=N, launches=launches)
+                op=op, v=v, v_host=v_host, y=y, work=work, inp=inp, N=N, launches=launches,
+                step_form=step_form)
 
 
 def main():
@@ -972,6 +980,7 @@ def main():
             "data": "synthetic",
             "config": {"workload": cfg["name"], "N": N, "m": m, "p": p, "h": h,
                        "variant": args.variant, "precision": args.precision,
+                       "step_form": R["step_form"],
                        "l2": "flushed between timed steps (256 MiB write)" if flush is not None
                        else "not flushed; basis working set > L2",
                        "parallelism": f"replicas x{world}"},

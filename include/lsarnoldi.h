@@ -116,7 +116,9 @@ typedef struct {
   float ms_combine;       /* device time of the output combination (phiv only) */
   int launches;           /* kernels this call launched */
   int arnoldi_kernel;     /* Arnoldi kernel that ran: 0 plain loads, 1 TMA-staged tile+halo,
-                             2 streaming (interior-only TMA stages); filled by lsa_arnoldi/lsa_phiv */
+                             2 streaming (interior-only TMA stages), 3 single thread-block
+                             cluster, 4 plain loads with the two-phase step (see
+                             lsa_tune_step); filled by lsa_arnoldi/lsa_phiv */
 } lsa_stats;
 
 /* Largest supported Krylov dimension m. */
@@ -157,6 +159,36 @@ lsa_status lsa_matvec(const lsa_op* op, const void* x, void* y, int precision,
 lsa_status lsa_arnoldi(const lsa_op* op, const double* v, int m, int variant, int precision,
                        void* V, double* H, void* work, size_t work_bytes,
                        lsa_stats* stats, void* stream);
+
+/* Step form of the grid Arnoldi kernel's hybrid variants (Alg. 4 with
+ * Algs. 5/6/7).  The one-pass form projects each tile together with its
+ * one-point halo (the halo values are projected again by the neighbouring
+ * tile), applies the stencil and forms the inner products, then reduces: one
+ * grid barrier per step.  The two-phase form projects every value once, waits
+ * at a grid barrier without a reduction, then reads the projected vector back
+ * with its halo for the stencil and the inner products: no repeated
+ * projection work, one more barrier per step.  Both compute bitwise the same
+ * basis and H.
+ * lsa_tune_step times both forms of lsa_arnoldi's Arnoldi kernel on
+ * (op, m, variant, precision) and records the faster one; later lsa_arnoldi,
+ * lsa_phiv and lsa_phiv_host calls on the current device with the same
+ * operator kind and grid, m, variant and precision use it (process-wide
+ * table, thread-safe).  LSA_TWO_PHASE=0 or 1 in the environment overrides the
+ * table.  Without either, the two-phase form runs on 3D grids and on float64
+ * 2D grids of at least six 16 x 16 tiles per SM, the one-pass form otherwise
+ * (the crossover measured on GB300).
+ *  v      dev, N doubles: start vector of the timing runs (not modified).
+ *  work   dev workspace of lsa_workspace_bytes(op, m, 0, precision).
+ *  reps   timed runs per form (>= 1; one untimed run precedes them).
+ *  two_phase  out (may be NULL): 1 if the two-phase form was recorded.
+ *  ms_one, ms_two  out (may be NULL): best Arnoldi kernel time of each form
+ *         in ms.
+ * When the forms do not apply (the variant is not hybrid, or the call would
+ * run the TMA, streaming or cluster kernel) nothing is timed or recorded and
+ * the outputs are 0.  Synchronises the stream. */
+lsa_status lsa_tune_step(const lsa_op* op, const double* v, int m, int variant, int precision,
+                         void* work, size_t work_bytes, int reps, int* two_phase, float* ms_one,
+                         float* ms_two, void* stream);
 
 /* phi products y_k = phi_k(h A) v, k = 0..p (Sect. 2.2, Eq. 13 with the phi
  * augmentation of Sect. 2.1).

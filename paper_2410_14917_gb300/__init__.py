@@ -210,6 +210,24 @@ def phiv_host(op: Operator, v_host: torch.Tensor, h: float, p: int, m: int, y_ho
     return _check(st, "lsa_phiv_host")
 
 
+def tune_step(op: Operator, v: torch.Tensor, m: int, variant="hcwy", precision="fp64", reps: int = 3,
+              work=None, stream=None):
+    """Times the one-pass and the two-phase hybrid step of the grid Arnoldi
+    kernel on (op, m, variant, precision) (lsa_tune_step) and records the
+    faster form for later calls with that shape.  Returns (two_phase, ms_one,
+    ms_two); (0, 0.0, 0.0) when the forms do not apply."""
+    if v.dtype != torch.float64 or not v.is_cuda or not v.is_contiguous() or v.numel() != op.N:
+        raise ValueError("v must be a contiguous float64 CUDA tensor of N values")
+    m = min(int(m), op.N)
+    work = work or Workspace.for_call(op, m, 0, precision)
+    two, a, b = ctypes.c_int(), ctypes.c_float(), ctypes.c_float()
+    st = B.lib().lsa_tune_step(ctypes.byref(op.c), _ptr(v), m, VARIANTS[variant], PRECISIONS[precision],
+                               ctypes.c_void_p(work.ptr), work.nbytes, int(reps), ctypes.byref(two),
+                               ctypes.byref(a), ctypes.byref(b), _stream_ptr(stream))
+    _check(st, "lsa_tune_step", ok=(B.LSA_OK,))
+    return two.value, a.value, b.value
+
+
 def probe_fp64_fma_tflops(iters: int = 2000, reps: int = 10, device="cuda"):
     """Measured float64 FMA throughput (TFLOP/s, best of reps) of
     lsa_probe_fp64_fma, timed with CUDA events on the current stream."""

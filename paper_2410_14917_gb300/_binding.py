@@ -8,7 +8,7 @@ from __future__ import annotations
 
 import ctypes
 import os
-from ctypes import POINTER, c_double, c_int, c_longlong, c_size_t, c_void_p, c_char_p
+from ctypes import POINTER, c_char_p, c_double, c_float, c_int, c_longlong, c_size_t, c_void_p
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "liblsarnoldi.so")
@@ -66,6 +66,8 @@ SIGNATURES = {
     "lsa_phiv_host": (c_int, [POINTER(LsaOp), c_void_p, c_double, c_int, c_int, c_double, c_int, c_int,
                               c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "lsa_probe_fp64_fma": (c_int, [c_int, c_void_p, POINTER(c_double), c_void_p]),
+    "lsa_tune_step": (c_int, [POINTER(LsaOp), c_void_p, c_int, c_int, c_int, c_void_p, c_size_t, c_int,
+                              POINTER(c_int), POINTER(c_float), POINTER(c_float), c_void_p]),
     "lsa_rhs": (c_int, [POINTER(LsaOp), c_void_p, c_void_p, c_void_p]),
     "lsa_axpby": (c_int, [c_longlong, c_double, c_void_p, c_double, c_void_p, c_void_p, c_void_p]),
     "lsa_expm_phi": (c_int, [c_void_p, c_int, c_int, c_double, c_int, c_void_p, c_void_p, c_size_t,

@@ -4,6 +4,9 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <map>
+#include <mutex>
+
 #include "lsa_internal.cuh"
 
 namespace lsa {
@@ -197,11 +200,75 @@ static bool use_cluster(const ArnoldiParams& P, int precision) {
   return c > 0;
 }
 
-static int arnoldi_kernel_kind(const ArnoldiParams& P, int precision) {
-  return use_cluster(P, precision) ? 3 : use_stream(P, precision) ? 2 : use_tma(P, precision) ? 1 : 0;
+// Two-phase step of the grid kernel's hybrid variants (project; grid
+// barrier; stencil and inner products: no halo projection, one more barrier
+// per step).  Chosen per device, operator shape, m, variant and precision:
+// LSA_TWO_PHASE=0/1 in the environment forces it; otherwise the form that
+// lsa_tune_step recorded for the shape; otherwise a default measured on
+// GB300: two-phase for 3D grids (the z-halo planes make the repeated
+// projection large) and for float64 2D grids with at least six 16x16 tiles
+// per SM, one-pass below that (the extra barrier costs more than the halo).
+struct StepKey {
+  int dev, kind, nx, ny, nz, m, variant, precision;
+  bool operator<(const StepKey& o) const {
+    const int a[8] = {dev, kind, nx, ny, nz, m, variant, precision};
+    const int b[8] = {o.dev, o.kind, o.nx, o.ny, o.nz, o.m, o.variant, o.precision};
+    for (int i = 0; i < 8; ++i)
+      if (a[i] != b[i]) return a[i] < b[i];
+    return false;
+  }
+};
+static std::mutex g_step_mu;
+static std::map<StepKey, int> g_step_choice;
+static thread_local int g_step_force = -1;     // set by lsa_tune_step around its timing runs
+
+static bool step_key(const ArnoldiParams& P, int precision, StepKey* k) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  *k = StepKey{dev, P.op.kind, P.op.nx, P.op.ny, P.op.nz, P.m, P.variant, precision};
+  return true;
 }
 
+static bool two_phase_applies(const ArnoldiParams& P, int precision) {
+  return is_hybrid(P.variant) && P.naug == 0 && !use_cluster(P, precision) &&
+         !use_stream(P, precision) && !use_tma(P, precision);
+}
+
+static int two_phase_choice(const ArnoldiParams& P, int precision) {
+  if (!two_phase_applies(P, precision)) return 0;
+  if (g_step_force >= 0) return g_step_force;
+  const char* env = getenv("LSA_TWO_PHASE");
+  if (env && (env[0] == '0' || env[0] == '1')) return env[0] - '0';
+  StepKey k;
+  if (!step_key(P, precision, &k)) return 0;
+  {
+    std::lock_guard<std::mutex> lock(g_step_mu);
+    auto it = g_step_choice.find(k);
+    if (it != g_step_choice.end()) return it->second;
+  }
+  if (P.op.nz > 1) return 1;
+  return (precision == LSA_FP64 && P.tl.ntiles >= 6 * sm_count()) ? 1 : 0;
+}
+
+static int arnoldi_kernel_kind(const ArnoldiParams& P, int precision) {
+  if (use_cluster(P, precision)) return 3;
+  if (use_stream(P, precision)) return 2;
+  if (use_tma(P, precision)) return 1;
+  return two_phase_choice(P, precision) ? 4 : 0;
+}
+
+static cudaError_t launch_arnoldi_grid(const ArnoldiParams& P, int precision, int G, cudaStream_t s);
+
 cudaError_t launch_arnoldi(const ArnoldiParams& P, int precision, int G, cudaStream_t s) {
+  if (P.two_phase == 0 && two_phase_choice(P, precision)) {
+    ArnoldiParams Q = P;
+    Q.two_phase = 1;
+    return launch_arnoldi_grid(Q, precision, G, s);
+  }
+  return launch_arnoldi_grid(P, precision, G, s);
+}
+
+static cudaError_t launch_arnoldi_grid(const ArnoldiParams& P, int precision, int G, cudaStream_t s) {
   if (use_cluster(P, precision)) return launch_arnoldi_cluster_advdiff2d(P, nullptr, nullptr, s);
   if (use_stream(P, precision)) {
     if (P.op.kind == LSA_OP_ADVDIFF2D) return launch_arnoldi_stream_advdiff2d(P, s);
@@ -514,6 +581,76 @@ lsa_status lsa_phiv(const lsa_op* op, const double* v, double h, int p, int m, d
     stats->arnoldi_kernel = arnoldi_kernel_kind(P, precision);
     return r;
   }
+  return LSA_OK;
+}
+
+lsa_status lsa_tune_step(const lsa_op* op, const double* v, int m, int variant, int precision,
+                         void* work, size_t work_bytes, int reps, int* two_phase, float* ms_one,
+                         float* ms_two, void* stream) {
+  if (two_phase) *two_phase = 0;
+  if (ms_one) *ms_one = 0.f;
+  if (ms_two) *ms_two = 0.f;
+  if (!v) return LSA_ERR_ARG;
+  if (variant < LSA_MGS || variant > LSA_IOCGS) return LSA_ERR_ARG;
+  const long long N = lsa_op_dof(op);
+  if (N < 1 || m < 1) return LSA_ERR_ARG;
+  if (m > N) m = (int)N;
+  if (reps < 1) reps = 1;
+  Prepared pr;
+  lsa_status st = prepare(op, m, precision, work, work_bytes, &pr);
+  if (st != LSA_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  ArnoldiParams P = pr.P;
+  P.vin = v;
+  P.variant = variant;
+  P.write_vlast = 0;
+  if (!two_phase_applies(P, precision)) return LSA_OK;
+  StepKey key;
+  if (!step_key(P, precision, &key)) return LSA_ERR_CUDA;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return LSA_ERR_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return LSA_ERR_CUDA;
+  }
+  float best[2] = {1e30f, 1e30f};
+  lsa_status result = LSA_OK;
+  for (int form = 0; form < 2 && result == LSA_OK; ++form) {
+    g_step_force = form;
+    for (int r = 0; r <= reps; ++r) {           // r = 0: warm-up
+      cudaError_t e = launch_init(P.ctl, pr.d, (float*)pr.d.g0, (float*)pr.d.g1, precision, P.H,
+                                  (m + 1) * m, v, P.V, s, nullptr);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+      if (e == cudaSuccess) e = launch_arnoldi(P, precision, pr.L.G, s);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (e != cudaSuccess) {
+        result = LSA_ERR_CUDA;
+        break;
+      }
+      lsa_stats one;
+      const lsa_status rs = fill_stats(P.ctl, &one, s);
+      if (rs < 0) {
+        result = rs;
+        break;
+      }
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      if (r > 0 && t < best[form]) best[form] = t;
+    }
+  }
+  g_step_force = -1;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (result != LSA_OK) return result;
+  const int choice = best[1] < best[0] ? 1 : 0;
+  {
+    std::lock_guard<std::mutex> lock(g_step_mu);
+    g_step_choice[key] = choice;
+  }
+  if (two_phase) *two_phase = choice;
+  if (ms_one) *ms_one = best[0];
+  if (ms_two) *ms_two = best[1];
   return LSA_OK;
 }
 

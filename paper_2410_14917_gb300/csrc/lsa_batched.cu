@@ -274,13 +274,16 @@ lsa_status lsa_batch_create(const lsa_op* ops, const int* m, int count, double h
   std::iota(b->order.begin(), b->order.end(), 0);
   std::stable_sort(b->order.begin(), b->order.end(),
                    [&](int a, int c) { return b->cost[a] > b->cost[c]; });
-  // default tiling: instances costlier than one CTA's fair share of the total
-  // go to groups of 4 CTAs
-  const double total = std::accumulate(b->cost.begin(), b->cost.end(), 0.0);
-  int nl = 0;
-  while (nl < count && b->cost[b->order[nl]] > total / b->G) ++nl;
-  b->nlarge = nl;
+  // default tiling: groups of 4 CTAs take every instance (in cost order) that
+  // has at least one tile per CTA of the group; single CTAs take the rest.
+  // (On the 512-instance advection-diffusion batch this is the tuner's pick
+  // for both precisions; a single CTA per instance leaves the largest ones as
+  // a long tail.)
   b->gsize = b->G >= 4 ? 4 : 1;
+  int nl = 0;
+  if (b->gsize > 1)
+    while (nl < count && b->inst[b->order[nl]].tl.ntiles >= b->gsize) ++nl;
+  b->nlarge = nl;
   if (b->nlarge == 0) b->gsize = 1;
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = cudaMemcpyAsync(b->w + b->BL.inst, b->inst.data(), (size_t)count * sizeof(BatchInst),
@@ -395,7 +398,7 @@ lsa_status lsa_batch_tune(lsa_batch* b, const double* v, double* y, int reps, in
   std::vector<Cand> cands;
   cands.push_back({1, 0});                       // one CTA per instance
   cands.push_back({b->G, b->count});             // the whole grid per instance
-  const int fr[] = {64, 32, 16, 8, 4, 2};
+  const int fr[] = {64, 32, 16, 8, 4, 2, 1};
   for (int g = 2; g <= 32 && g <= b->G / 2; g *= 2)
     for (int f : fr) {
       int nl = b->count / f;

@@ -102,6 +102,7 @@ __device__ __noinline__ bool batch_instance(const BatchParams& BP, const BatchIn
     P.m = I.m;
     P.variant = BP.variant;
     P.write_vlast = 0;
+    P.two_phase = 0;
     P.brk_tol = BP.brk_tol;
     P.timeout_ns = BP.timeout_ns;
     SP.H = I.H;

@@ -148,35 +148,56 @@ struct ClusterEngine {
       Vt[(size_t)wout * CL_TP + t] = w;
     }
     // self terms: block sums
-    double s3[3] = {(self & SELF_XX) ? x * x : 0.0, (self & SELF_XW) ? x * w : 0.0,
-                    (self & SELF_WW) ? w * w : 0.0};
-#pragma unroll
-    for (int k = 0; k < 3; ++k) s3[k] = warp_sum(s3[k]);
-    if (e.lane == 0) {
-      e.S.bred[e.warp][0] = s3[0];
-      e.S.bred[e.warp][1] = s3[1];
-      e.S.bred[e.warp][2] = s3[2];
+    double s3[4] = {(self & SELF_XX) ? x * x : 0.0, (self & SELF_XW) ? x * w : 0.0,
+                    (self & SELF_WW) ? w * w : 0.0, 0.0};
+    {
+      const double r = warp_sum_many<4>(s3);   // lane l: value l >> 3
+      if ((e.lane & 7) == 0 && e.lane < 24) e.S.bred[e.warp][e.lane >> 3] = r;
     }
     __syncthreads();   // x, w and the warp sums are in shared memory
     const int nd = stencil ? ncp : 0;
     // inner products: warp <-> columns c = warp, warp + NW, ...; lane <-> points
-    for (int c = e.warp; c < nd; c += NW) {
-      const double* vc = Vt + (size_t)c * CL_TP;
-      const double* xc = Vt + (size_t)xout * CL_TP;
-      const double* wc = Vt + (size_t)wout * CL_TP;
-      double ax = 0.0, aw = 0.0;
+    const double* xc = Vt + (size_t)xout * CL_TP;
+    const double* wc = Vt + (size_t)wout * CL_TP;
+    if (nd <= NW) {              // at most one column per warp
+      const int c = e.warp;
+      if (c < nd) {
+        const double* vc = Vt + (size_t)c * CL_TP;
+        double ax = 0.0, aw = 0.0;
 #pragma unroll
-      for (int k = 0; k < CL_TP / 32; ++k) {
-        const int q = e.lane + 32 * k;
-        ax = fma(vc[q], xc[q], ax);
-        aw = fma(vc[q], wc[q], aw);
+        for (int k = 0; k < CL_TP / 32; ++k) {
+          const int q = e.lane + 32 * k;
+          ax = fma(vc[q], xc[q], ax);
+          aw = fma(vc[q], wc[q], aw);
+        }
+        ax = warp_sum(ax);
+        aw = warp_sum(aw);
+        if (e.lane == 0) {
+          part[c] = ax;
+          part[nd + c] = aw;
+        }
       }
-      ax = warp_sum(ax);
-      aw = warp_sum(aw);
-      if (e.lane == 0) {
-        part[c] = ax;
-        part[nd + c] = aw;
+    } else {                     // all the warp's columns, then one transposed warp sum
+      double v[2 * KMAX];
+#pragma unroll
+      for (int kk = 0; kk < KMAX; ++kk) {
+        const int c = e.warp + NW * kk;
+        double ax = 0.0, aw = 0.0;
+        if (c < nd) {
+          const double* vc = Vt + (size_t)c * CL_TP;
+#pragma unroll
+          for (int k = 0; k < CL_TP / 32; ++k) {
+            const int q = e.lane + 32 * k;
+            ax = fma(vc[q], xc[q], ax);
+            aw = fma(vc[q], wc[q], aw);
+          }
+        }
+        v[2 * kk] = ax;
+        v[2 * kk + 1] = aw;
       }
+      const double r = warp_sum_many<2 * KMAX>(v);   // lanes 2k, 2k+1: value k
+      const int k = e.lane >> 1, c = e.warp + NW * (k >> 1);
+      if ((e.lane & 1) == 0 && c < nd) part[(k & 1) ? nd + c : c] = r;
     }
     if (e.tid < 3) {
       double acc = 0.0;

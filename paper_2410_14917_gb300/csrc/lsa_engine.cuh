@@ -219,6 +219,67 @@ struct Engine {
     }
   }
 
+  // First pass of the two-phase step: x = a*src - sum_c coef_c V_c on this
+  // CTA's contiguous share of the N values (all species; equal shares, so
+  // every CTA has the same work), stored to ps.xout; no halo, no shared
+  // memory, no barrier.  Each value goes through the same operations in the
+  // same order as in project_plane (CB-column batches, the two alternating
+  // accumulators, then the tail), so the stored x is bitwise the value the
+  // one-pass step stores.
+  __device__ void project_flat(const PassT<B>& ps) {
+    constexpr int U = 4;                       // values per thread per round
+    constexpr int CB = F64 ? 4 : 8;
+    const long long N = P.op.N;
+    long long per = (N + gsize - 1) / gsize;
+    per = (per + 31) & ~31LL;                  // shares start on a 32-value boundary
+    const long long e0 = (long long)grank * per;
+    const long long e1 = min(N, e0 + per);
+    const B* Vb = reinterpret_cast<const B*>(P.V);
+    const Tc a = (Tc)ps.a;
+    for (long long base = e0; base < e1; base += (long long)U * NT) {
+      long long gi[U];
+      Tc x[U], xb[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const long long q = base + tid + (long long)u * NT;
+        gi[u] = q < e1 ? q : e0;               // out-of-share lanes re-read a valid value
+        if (ps.src64) x[u] = a * (Tc)__ldg(ps.src64 + gi[u]);
+        else x[u] = a * (Tc)__ldcg(ps.srcB + gi[u]);
+        xb[u] = (Tc)0;
+      }
+      int c = ps.c0;
+      for (; c + CB <= ps.c1; c += CB) {
+        Tc v[CB][U];
+#pragma unroll
+        for (int i = 0; i < CB; ++i) {
+          const B* col = Vb + (long long)(c + i) * N;
+#pragma unroll
+          for (int u = 0; u < U; ++u) v[i][u] = (Tc)__ldcg(col + gi[u]);
+        }
+#pragma unroll
+        for (int i = 0; i < CB; ++i) {
+          const Tc cc = S.coefc[c + i];
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            if (i & 1) xb[u] = fma(-cc, v[i][u], xb[u]);
+            else x[u] = fma(-cc, v[i][u], x[u]);
+          }
+        }
+      }
+      for (; c < ps.c1; ++c) {
+        const Tc cc = S.coefc[c];
+        const B* col = Vb + (long long)c * N;
+#pragma unroll
+        for (int u = 0; u < U; ++u) x[u] = fma(-cc, (Tc)__ldcg(col + gi[u]), x[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const long long q = base + tid + (long long)u * NT;
+        if (q < e1) ps.xout[q] = (B)(x[u] + xb[u]);
+      }
+    }
+  }
+
   // Stencil at plane z (interior only) from the ring: w = A x.
   __device__ void stencil_plane(const PassT<B>& ps, int x0, int y0, int z, int w, int hg) {
     const DevOp& d = P.op;
@@ -427,25 +488,30 @@ struct Engine {
 
   // Per-CTA partial sums of a pass to HBM (dot slots, then the three self terms).
   __device__ int write_partials(const PassT<B>& ps) {
+    static_assert(KMAX == 8, "the transposed warp sum below takes 2*KMAX = 16 values");
     const int nd = ps.d1 > ps.d0 ? ps.d1 - ps.d0 : 0;
     double* part = P.partials + (long long)grank * SLOTS;
+    {
+      // the warp's 2*KMAX column sums at once: value 2kk is x . V_c, 2kk+1 is
+      // w . V_c for column c = d0 + warp + NW*kk; lanes 2k and 2k+1 get value k
+      double v[2 * KMAX];
 #pragma unroll
-    for (int kk = 0; kk < KMAX; ++kk) {
-      int c = ps.d0 + warp + NW * kk;
-      double vx, vw;
-      if constexpr (F64) { vx = ax[kk]; vw = aw[kk]; }
-      else { vx = (double)axs[kk] - (double)axc[kk]; vw = (double)aws[kk] - (double)awc[kk]; }
-      vx = warp_sum(vx);
-      vw = warp_sum(vw);
-      if (c < ps.d1 && lane == 0) {
-        if constexpr (AUG) {
-          if (grank == 0) {
-            vx += aug_dot(c, S.xi);
-            vw += aug_dot(c, S.xw);
-          }
+      for (int kk = 0; kk < KMAX; ++kk) {
+        if constexpr (F64) { v[2 * kk] = ax[kk]; v[2 * kk + 1] = aw[kk]; }
+        else {
+          v[2 * kk] = (double)axs[kk] - (double)axc[kk];
+          v[2 * kk + 1] = (double)aws[kk] - (double)awc[kk];
         }
-        part[c - ps.d0] = (ps.dmode & DOT_X) ? vx : 0.0;
-        part[nd + c - ps.d0] = (ps.dmode & DOT_W) ? vw : 0.0;
+      }
+      double r = warp_sum_many<2 * KMAX>(v);
+      const int k = lane >> 1, kk = k >> 1, isw = k & 1;
+      const int c = ps.d0 + warp + NW * kk;
+      if ((lane & 1) == 0 && c < ps.d1) {
+        if constexpr (AUG) {
+          if (grank == 0) r += isw ? aug_dot(c, S.xw) : aug_dot(c, S.xi);
+        }
+        if (isw) part[nd + c - ps.d0] = (ps.dmode & DOT_W) ? r : 0.0;
+        else part[c - ps.d0] = (ps.dmode & DOT_X) ? r : 0.0;
       }
     }
     if constexpr (!F64) {
@@ -453,8 +519,11 @@ struct Engine {
       sxw = (double)fxw[0] - (double)fxw[1];
       sww = (double)fww[0] - (double)fww[1];
     }
-    double a0 = warp_sum(sxx), a1 = warp_sum(sxw), a2 = warp_sum(sww);
-    if (lane == 0) { S.bred[warp][0] = a0; S.bred[warp][1] = a1; S.bred[warp][2] = a2; }
+    {
+      double t[4] = {sxx, sxw, sww, 0.0};
+      const double r = warp_sum_many<4>(t);   // lane l: value l >> 3
+      if ((lane & 7) == 0 && lane < 24) S.bred[warp][lane >> 3] = r;
+    }
     __syncthreads();
     if (tid < 3) {
       double acc = 0;
@@ -499,12 +568,19 @@ struct Engine {
     for (int s = tid; s < nslots; s += NT) {
       double acc = 0.0;
       int r = 0;
-      for (; r + 8 <= nrows; r += 8) {
-        double v[8];
+      for (; r + 16 <= nrows; r += 16) {
+        double v[16];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] = __ldcg(src + (long long)(r + i) * SLOTS + s);
+        for (int i = 0; i < 16; ++i) v[i] = __ldcg(src + (long long)(r + i) * SLOTS + s);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) acc += v[i];
+        for (int i = 0; i < 16; ++i) acc += v[i];
+      }
+      for (; r + 4 <= nrows; r += 4) {
+        double v[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v[i] = __ldcg(src + (long long)(r + i) * SLOTS + s);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc += v[i];
       }
       for (; r < nrows; ++r) acc += __ldcg(src + (long long)r * SLOTS + s);
       if (to_smem) dst[s] = acc;
@@ -551,13 +627,22 @@ struct Engine {
     return true;
   }
 
-  // Read the published control state into shared memory (all threads).
+  // Read the published control state into shared memory (all threads): the
+  // next pass's coefficients and flags, and the hybrid step's lazy scales,
+  // norm estimate, ||A v|| and reduction count, so that whichever CTA runs
+  // the next step finds them here (no L2 round trip inside the step).
   __device__ void load_ctl(int ncoef) {
-    for (int c = tid; c < ncoef; c += NT) S.coefc[c] = (Tc)__ldcg(&P.ctl->coef[c]);
+    for (int c = tid; c < ncoef; c += NT) {
+      S.coefc[c] = (Tc)__ldcg(&P.ctl->coef[c]);
+      S.sig[c] = __ldcg(&P.ctl->sigma[c]);
+    }
     if (tid == 0) {
       S.a = (Tc)__ldcg(&P.ctl->a);
       S.done = __ldcg(&P.ctl->done);
       S.fallback_pending = __ldcg(&P.ctl->fallback_pending);
+      S.nrm_est_c = __ldcg(&P.ctl->nrm_est);
+      S.aw_prev_c = __ldcg(&P.ctl->aw_prev);
+      S.syncs_c = __ldcg(&P.ctl->syncs);
     }
     __syncthreads();
   }
@@ -589,11 +674,33 @@ struct Engine {
       }
       fn();
       __syncthreads();
-      if (tid == 0) { P.ctl->barriers = __ldcg(&P.ctl->barriers) + 1; }
+      if (tid == 0) atomicAdd(&P.ctl->barriers, 1);
       barrier_release(br, gen);
     }
     ++gen;
     load_ctl(ncoef_after);
+    return true;
+  }
+
+  // Grid barrier without a reduction (between the two passes of the
+  // two-phase step), with the arrival structure of reduce_step.
+  __device__ bool sync_only(unsigned& gen) {
+    const BarrierRef br = arnoldi_barrier(P.ctl);
+    int r;
+    if (P.gsum == nullptr || gsize > RG * RG_MAX) {
+      r = barrier_arrive(br, gen, gsize, &S.flag, P.timeout_ns);
+    } else {
+      const int grp = grank / RG, g0 = grp * RG;
+      const int gn = min(RG, gsize - g0), ngr = (gsize + RG - 1) / RG;
+      const int lead = counter_arrive(&P.ctl->g_arrive[grp], gen, gn, &S.flag);
+      r = barrier_arrive(br, gen, ngr, &S.flag, P.timeout_ns, lead != 0);
+    }
+    if (r < 0) return false;
+    if (r == 1) {
+      if (tid == 0) atomicAdd(&P.ctl->barriers, 1);
+      barrier_release(br, gen);
+    }
+    ++gen;
     return true;
   }
 
@@ -624,14 +731,18 @@ struct Engine {
         ctl->m_eff = j - 1;
         S.flag = 1;
       } else {
-        double sj = 1.0 / sqrt(Gj);
+        // one reciprocal square root for both 1/||x|| and ||x|| (a float64
+        // warp instruction is slow on this GPU, and this thread is the
+        // critical path of the step)
+        const double sj = rsqrt(Gj);
+        const double nx = Gj * sj;
         S.sj = sj;
         if (j == 1) {
-          ctl->beta = sqrt(Gj);
+          ctl->beta = nx;
         } else {
-          const double ne_prev = cached ? S.nrm_est_c : __ldcg(&ctl->nrm_est);
-          const double aw_prev = cached ? S.aw_prev_c : __ldcg(&ctl->aw_prev);
-          double tn = ne_prev * sqrt(Gj);                  // true norm of the previous vector
+          const double ne_prev = S.nrm_est_c;
+          const double aw_prev = S.aw_prev_c;
+          double tn = ne_prev * nx;                        // true norm of the previous vector
           S.true_nrm = tn;
           if (!(tn > P.brk_tol * aw_prev)) {               // lagged breakdown test
             Hat(j - 1, j - 2) = tn;
@@ -646,13 +757,13 @@ struct Engine {
         temp2[np] = sj * sj * Pj;
         temp2[np + 1] = sj * sj * Q;
       }
-      ctl->syncs = cached ? ++S.syncs_c : __ldcg(&ctl->syncs) + 1;
+      ctl->syncs = ++S.syncs_c;
       if (cached && S.flag) S.done = 1;
     }
     __syncthreads();
     if (S.flag) return;
     for (int i = tid; i < np; i += NT) {
-      double si = cached ? S.sig[i] : __ldcg(&ctl->sigma[i]);
+      double si = S.sig[i];
       temp1[i] = si * S.sj * S.red[i];
       temp2[i] = si * S.sj * S.red[np + i];
     }
@@ -663,23 +774,27 @@ struct Engine {
       // New row of T (Alg. 5: T_{j,1:j-1} = -temp_{1:j-1,1}^T T_{1:j-1,1:j-1};
       // Alg. 6: T_{j,1:j-1} = -temp_{1:j-1,1}^T; for Alg. 7 this is M^{-1}).
       if (!cached) stage(P.T, np);   // cached: small already holds rows 0..np-1 of T
-      for (int k = tid; k < np; k += NT) {
-        double acc = -temp1[k];
-        if (P.variant != LSA_HNCWY) {
-          // four interleaved partial sums (fixed order: deterministic) shorten the chain
-          double a1 = 0.0, a2 = 0.0, a3 = 0.0, a4 = 0.0;
-          int i = k + 1;
-          for (; i + 3 < np; i += 4) {
-            a1 = fma(-temp1[i], small[i * MMAX + k], a1);
-            a2 = fma(-temp1[i + 1], small[(i + 1) * MMAX + k], a2);
-            a3 = fma(-temp1[i + 2], small[(i + 2) * MMAX + k], a3);
-            a4 = fma(-temp1[i + 3], small[(i + 3) * MMAX + k], a4);
-          }
-          for (; i < np; ++i) a1 = fma(-temp1[i], small[i * MMAX + k], a1);
-          acc += (a1 + a2) + (a3 + a4);
+      if (P.variant != LSA_HNCWY) {
+        // T_{j,k} = -temp1_k - sum_{i>k} temp1_i T_{i,k}: the four lanes
+        // 4k..4k+3 (all eight warps) take the terms i = k+1+q, k+5+q, ...
+        // and combine their sums in a fixed order (deterministic)
+        static_assert(MMAX * 4 <= NT, "four lanes per column");
+        const int k = tid >> 2, q = tid & 3;
+        double a = 0.0;
+        if (k < np)
+          for (int i = k + 1 + q; i < np; i += 4) a = fma(-temp1[i], small[i * MMAX + k], a);
+        a += __shfl_xor_sync(0xffffffffu, a, 1);
+        a += __shfl_xor_sync(0xffffffffu, a, 2);
+        if (k < np && q == 0) {
+          const double acc = -temp1[k] + a;
+          small[np * MMAX + k] = acc;
+          P.T[np * MMAX + k] = acc;
         }
-        small[np * MMAX + k] = acc;
-        P.T[np * MMAX + k] = acc;
+      } else {
+        for (int k = tid; k < np; k += NT) {
+          small[np * MMAX + k] = -temp1[k];
+          P.T[np * MMAX + k] = -temp1[k];
+        }
       }
       __syncthreads();
       if (P.variant != LSA_HGSMGS) {
@@ -734,7 +849,9 @@ struct Engine {
         S.nrm_est_c = 1.0;
         if (cached) S.fallback_pending = 1;
       } else {
-        double ne = sqrt(t - S.ss);           // Eq. 18
+        const double d = t - S.ss;            // Eq. 18: ne = sqrt(d), scale = 1/ne
+        const double rd = (d > 0.0) ? rsqrt(d) : 0.0;
+        const double ne = d * rd;
         if (!(ne > P.brk_tol * awn)) {
           Hat(j, j - 1) = ne;
           ctl->m_eff = j;
@@ -744,7 +861,7 @@ struct Engine {
         }
         ctl->nrm_est = ne;
         S.nrm_est_c = ne;
-        S.scale = (ne > 0.0) ? 1.0 / ne : 0.0;
+        S.scale = rd;
       }
       ctl->aw_prev = awn;
       S.aw_prev_c = awn;
@@ -757,7 +874,7 @@ struct Engine {
     }
     __syncthreads();
     for (int i = tid; i < j; i += NT) {
-      double si = (i == j - 1) ? S.sj : (cached ? S.sig[i] : __ldcg(&ctl->sigma[i]));
+      double si = (i == j - 1) ? S.sj : S.sig[i];
       const double c = si * hcol[i] * S.scale;
       ctl->coef[i] = c;
       if (cached) S.coefc[i] = (Tc)c;
@@ -788,14 +905,22 @@ struct Engine {
     __syncthreads();
   }
 
-  // out[r] = in[r] + sum_{k<r} small[r][k] in[k]  (unit lower-triangular times vector), r < n
+  // out[r] = in[r] + sum_{k<r} small[r][k] in[k]  (unit lower-triangular times
+  // vector), r < n: warp w takes rows w, w+NW, ..., then one transposed warp sum.
   __device__ void apply_unit_lower(const double* in, double* out, int n) {
-    for (int r = warp; r < n; r += NW) {
-      double acc = 0.0;
-      for (int k = lane; k < r; k += 32) acc = fma(small[r * MMAX + k], in[k], acc);
-      acc = warp_sum(acc);
-      if (lane == 0) out[r] = in[r] + acc;
+    static_assert(MMAX <= 8 * NW, "eight rows per warp");
+    double acc[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int r = warp + NW * i;
+      double a = 0.0;
+      if (r < n)
+        for (int k = lane; k < r; k += 32) a = fma(small[r * MMAX + k], in[k], a);
+      acc[i] = a;
     }
+    const double sum = warp_sum_many<8>(acc);   // lane l: row warp + NW*(l >> 2)
+    const int r = warp + NW * (lane >> 2);
+    if ((lane & 3) == 0 && r < n) out[r] = in[r] + sum;
     __syncthreads();
   }
 
@@ -803,8 +928,8 @@ struct Engine {
     Ctl* ctl = P.ctl;
     if (tid == 0) {
       double nrm = sqrt(S.red[0]);
-      ctl->syncs = cached ? ++S.syncs_c : __ldcg(&ctl->syncs) + 1;
-      if (!(nrm > P.brk_tol * (cached ? S.aw_prev_c : __ldcg(&ctl->aw_prev)))) {
+      ctl->syncs = ++S.syncs_c;
+      if (!(nrm > P.brk_tol * S.aw_prev_c)) {
         Hat(j, j - 1) = nrm;
         ctl->m_eff = j;
         ctl->breakdown = 1;
@@ -831,12 +956,12 @@ struct Engine {
     if (tid == 0) {
       const int m = P.m;
       double nrm = sqrt(S.red[0]);
-      double hl = (cached ? S.nrm_est_c : __ldcg(&ctl->nrm_est)) * nrm;   // true norm of the projected v_{m+1}
+      double hl = S.nrm_est_c * nrm;   // true norm of the projected v_{m+1}
       Hat(m, m - 1) = hl;
       ctl->h_last = hl;
       ctl->sigma[m] = (nrm > 0.0) ? 1.0 / nrm : 0.0;
-      ctl->syncs = cached ? ++S.syncs_c : __ldcg(&ctl->syncs) + 1;
-      if (!(hl > P.brk_tol * (cached ? S.aw_prev_c : __ldcg(&ctl->aw_prev)))) ctl->breakdown = 1;
+      ctl->syncs = ++S.syncs_c;
+      if (!(hl > P.brk_tol * S.aw_prev_c)) ctl->breakdown = 1;
     }
   }
 
@@ -851,8 +976,13 @@ struct Engine {
     const long long N = P.op.N;
     const int m = P.m;
     unsigned gen = 0;
-    if (tid == 0) { S.a = (Tc)1; S.done = 0; S.fallback_pending = 0; }
+    if (tid == 0) { S.a = (Tc)1; S.done = 0; S.fallback_pending = 0; S.syncs_c = 0; }
     __syncthreads();
+    // Two-phase form: a pass over equal flat shares projects x_j (no halo),
+    // a grid barrier, then the tile pass reads x_j back with its halo for
+    // w_j = A x_j and the inner products.  Every value goes through the same
+    // operations in the same order as in the one-pass form.
+    const bool two = P.two_phase != 0 && !AUG && !cached;
     for (int j = 1; j <= m; ++j) {
       PassT<B> ps;
       ps.c0 = 0; ps.c1 = j - 1;
@@ -864,6 +994,15 @@ struct Engine {
       ps.d0 = 0; ps.d1 = j - 1;
       ps.dmode = DOT_X | DOT_W;
       ps.self = SELF_XX | SELF_XW | SELF_WW;
+      if (two) {
+        project_flat(ps);                      // x_j (no halo)
+        if (!sync_only(gen)) return;
+        ps.c0 = ps.c1 = 0;                     // then x_j with its halo, w_j = A x_j, the products
+        ps.a = 1.0;
+        ps.src64 = nullptr;
+        ps.srcB = ps.xout;
+        ps.xout = nullptr;
+      }
       int ns = run_pass(ps);
       if (!reduce_step(gen, ns, j, [&] { hybrid_step(j); })) return;
       if (S.done) return;

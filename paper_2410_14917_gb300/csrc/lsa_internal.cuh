@@ -98,6 +98,8 @@ struct ArnoldiParams {
   int m;
   int variant;
   int write_vlast;         // MGS/CGS2: write v_{m+1} (Arnoldi output only)
+  int two_phase;           // hybrid: project, grid barrier, then stencil and inner products
+                           // (no halo projection; one more barrier per step)
   double brk_tol;
   long long timeout_ns;
   float* E;                // streaming float32 kernel: edge array, (m+3) columns of N/8 (or null)
@@ -193,6 +195,32 @@ __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
+}
+
+// Warp sums of NV per-lane values at once (NV a power of two, at most 32):
+// recursive halving, each stage trading half of the values still held with
+// the partner lane and adding the other half, so a lane does NV - 1 + (5 -
+// log2 NV) additions instead of 5 per value (float64 additions are scarce on
+// this GPU).  On return lane l holds the sum of value l >> (5 - log2 NV).
+template <int NV>
+__device__ __forceinline__ double warp_sum_many(double (&v)[NV]) {
+  static_assert(NV >= 1 && NV <= 32 && (NV & (NV - 1)) == 0, "NV must be a power of two <= 32");
+  const unsigned lane = threadIdx.x & 31u;
+  int s = 16;
+#pragma unroll
+  for (int h = NV / 2; h >= 1; h >>= 1, s >>= 1) {
+    const bool up = (lane & (unsigned)s) != 0u;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const double send = up ? v[i] : v[i + h];
+      const double keep = up ? v[i + h] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+    }
+  }
+  double r = v[0];
+#pragma unroll
+  for (; s >= 1; s >>= 1) r += __shfl_xor_sync(0xffffffffu, r, s);
+  return r;
 }
 
 // Grid barrier with a bounded wait.  All `count` participating CTAs call it

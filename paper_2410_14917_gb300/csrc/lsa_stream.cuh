@@ -681,7 +681,7 @@ struct StreamEngine {
     const int m = e.P.m;
     const int wc = sp.wcol;
     unsigned gen = 0;
-    if (e.tid == 0) { e.S.a = 1.f; e.S.done = 0; e.S.fallback_pending = 0; *s_stop = 0; }
+    if (e.tid == 0) { e.S.a = 1.f; e.S.done = 0; e.S.fallback_pending = 0; e.S.syncs_c = 0; *s_stop = 0; }
     __syncthreads();
     int j = 1, kind = 0;
     for (;;) {

@@ -590,7 +590,7 @@ struct TmaEngine {
     const int m = e.P.m;
     const int wc = tp.wcol;
     unsigned gen = 0;
-    if (e.tid == 0) { e.S.a = (Tc)1; e.S.done = 0; e.S.fallback_pending = 0; }
+    if (e.tid == 0) { e.S.a = (Tc)1; e.S.done = 0; e.S.fallback_pending = 0; e.S.syncs_c = 0; }
     __syncthreads();
     for (int j = 1; j <= m; ++j) {
       TmaPass ps;

@@ -1,0 +1,141 @@
+"""The two-phase hybrid step of the grid Arnoldi kernel (Alg. 4 with Algs.
+5/6/7: project every value once over equal flat shares, grid barrier, then
+stencil and inner products) against the one-pass step, which projects each
+tile's halo again.  Both apply the same operations in the same order to every
+value, so basis, H and phi products must agree bit for bit; the two-phase form
+is also checked against the oracle, on ragged grids (partial tiles and flat
+shares), 2D and 3D operators, both precisions and each hybrid correction, and
+the step-form tuner's choice is the form later calls report."""
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from tests.gpu_util import FP32_TOL, FP64_TOL, device_inputs, oracle_phiv, rel_errors
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+CASES = [W.advdiff2d(64, m=30, p=2), W.advdiff2d(40, ny=23, m=24, p=1),
+         W.grayscott2d(40, m=32, p=2), W.adr3d(20, m=24, p=1),
+         W.advdiff2d(3, ny=5, m=6, p=1)]
+VARIANTS = ["hcwy", "hncwy", "hgsmgs"]
+
+
+class env:
+    """Set environment variables for the duration of a block."""
+
+    def __init__(self, **kw):
+        self.kw = kw
+
+    def __enter__(self):
+        self.old = {k: os.environ.get(k) for k in self.kw}
+        os.environ.update({k: str(v) for k, v in self.kw.items()})
+
+    def __exit__(self, *a):
+        for k, v in self.old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
+def _op(cfg):
+    import paper_2410_14917_gb300 as lsa
+
+    inp = W.make_inputs(cfg)
+    v, fields = device_inputs(cfg, inp, torch)
+    return lsa.Operator.from_workload(cfg, fields), v
+
+
+def _grid_kernel_env(two):
+    # the float32-basis form would otherwise run the TMA or streaming kernels
+    return env(LSA_TWO_PHASE=int(two), LSA_TMA=0, LSA_STREAM=0, LSA_CLUSTER=0)
+
+
+@pytest.mark.parametrize("cfg", CASES, ids=[c["name"] for c in CASES])
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_two_phase_arnoldi_bitwise_equal_to_one_pass(cfg, variant, precision):
+    import paper_2410_14917_gb300 as lsa
+
+    op, v = _op(cfg)
+    m = min(cfg["m"], op.N)
+    out = {}
+    for two in (0, 1):
+        with _grid_kernel_env(two):
+            V, H, st = lsa.arnoldi(op, v, m, variant=variant, precision=precision)
+        out[two] = (V.cpu().numpy(), H.cpu().numpy(), st)
+    (V0, H0, s0), (V1, H1, s1) = out[0], out[1]
+    assert s0["arnoldi_kernel"] == 0 and s1["arnoldi_kernel"] == 4
+    assert s0["status"] == s1["status"] == 0 and s0["m_eff"] == s1["m_eff"] == m
+    assert np.array_equal(H0, H1)
+    assert np.array_equal(V0, V1)
+    assert s0["norm_fallbacks"] == s1["norm_fallbacks"]
+    for s in (s0, s1):
+        assert s["grid_syncs"] == m + 1 + s["norm_fallbacks"]
+    # one barrier without a reduction per step, plus one per reduction
+    assert s1["grid_barriers"] == s1["grid_syncs"] + m
+    assert s0["grid_barriers"] == s0["grid_syncs"]
+
+
+@pytest.mark.parametrize("cfg", CASES[:4], ids=[c["name"] for c in CASES[:4]])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_two_phase_phiv_matches_oracle(cfg, precision):
+    import paper_2410_14917_gb300 as lsa
+
+    op, v = _op(cfg)
+    with _grid_kernel_env(1):
+        y1, st = lsa.phiv(op, v, cfg["h"], cfg["p"], cfg["m"], variant="hcwy", precision=precision)
+    with _grid_kernel_env(0):
+        y0, _ = lsa.phiv(op, v, cfg["h"], cfg["p"], cfg["m"], variant="hcwy", precision=precision)
+    assert st["arnoldi_kernel"] == 4
+    ref, info = oracle_phiv(cfg, "hcwy")
+    tol = FP64_TOL if precision == "fp64" else FP32_TOL
+    assert torch.equal(y0, y1)
+    assert max(rel_errors(y1, ref)) < tol
+    assert st["m_eff"] == info["m_eff"]
+    assert st["grid_syncs"] == cfg["m"] + 1 + st["norm_fallbacks"]
+
+
+def test_two_phase_headline_shape_sampled():
+    """Gray-Scott 512^2 with m = 64 (the full-size float64 workload): both
+    forms agree bit for bit, and the Arnoldi relation holds on sampled
+    columns of the two-phase basis."""
+    import paper_2410_14917_gb300 as lsa
+
+    cfg = W.config(1)
+    op, v = _op(cfg)
+    m = cfg["m"]
+    res = {}
+    for two in (0, 1):
+        with _grid_kernel_env(two):
+            V, H, st = lsa.arnoldi(op, v, m, variant="hcwy")
+        res[two] = (V, H, st)
+    assert res[1][2]["arnoldi_kernel"] == 4
+    assert torch.equal(res[0][1], res[1][1]) and torch.equal(res[0][0], res[1][0])
+    V, H = res[1][0], res[1][1]
+    for j in (0, 17, m - 1):
+        Av = lsa.matvec(op, V[:, j].contiguous())
+        r = Av - V @ H[:, j]
+        assert float(r.norm() / Av.norm()) < 1e-11
+
+
+def test_tune_step_records_choice():
+    import paper_2410_14917_gb300 as lsa
+
+    cfg = W.grayscott2d(128, m=24, p=1)
+    op, v = _op(cfg)
+    os.environ.pop("LSA_TWO_PHASE", None)
+    two, ms1, ms2 = lsa.tune_step(op, v, cfg["m"], variant="hcwy", precision="fp64", reps=2)
+    assert two in (0, 1) and ms1 > 0 and ms2 > 0
+    assert two == (1 if ms2 < ms1 else 0)
+    _, st = lsa.phiv(op, v, cfg["h"], cfg["p"], cfg["m"], variant="hcwy")
+    assert st["arnoldi_kernel"] == (4 if two else 0)
+    # the environment overrides the recorded choice
+    with env(LSA_TWO_PHASE=1 - two):
+        _, st = lsa.phiv(op, v, cfg["h"], cfg["p"], cfg["m"], variant="hcwy")
+    assert st["arnoldi_kernel"] == (0 if two else 4)
+    # variants without the hybrid step: nothing to choose
+    assert lsa.tune_step(op, v, cfg["m"], variant="mgs") == (0, 0.0, 0.0)
