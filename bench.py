@@ -45,8 +45,13 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) of one launch of the dominant kernel from an ncu
 # capture of the current kernel, keyed by workload, precision, variant and
 # Arnoldi kernel kind (0 one-pass, 4 two-phase grid kernel, 2 streaming);
-# a workload without an up-to-date capture reports null.
-PROFILED_TRAFFIC = {}
+# a workload without an up-to-date capture reports null.  Gray-Scott 512^2:
+# profiles/k_arnoldi_grayscott2d_512_fp64.md (both step forms); the 3D line's
+# capture is of the 192^3 case (same tiling), scaled by the unknowns
+# ((256/192)^3) (profiles/k_arnoldi_stream_adr3d_192_fp32.md).
+PROFILED_TRAFFIC = {("grayscott2d_512", "fp64", "hcwy", 0): 9.118409e9 + 0.744297e9,
+                    ("grayscott2d_512", "fp64", "hcwy", 4): 13.717263e9 + 0.777655e9,
+                    ("adr3d_256", "fp32", "hcwy", 2): (28.712327e9 + 2.551436e9) * (256 / 192) ** 3}
 
 
 def parse():
@@ -441,7 +446,8 @@ def bench_batched(args, world, rank, local, bcfg):
                        "variant": args.variant, "precision": args.precision,
                        "N_total": int(b.v_elems), "ctas": b.ctas,
                        "tiling": {"group_size": gs, "nlarge": nl, "tuned_ms": ms_tune,
-                                  "tune_s": t_tune, "default": list(default_tiling)},
+                                  "tune_s": t_tune, "default": list(default_tiling),
+                                  "step_form": "two-phase" if b.step_form else "one-pass"},
                        "graph": True,
                        "l2": "flushed between timed steps (256 MiB write)" if flush is not None
                        else "not flushed",

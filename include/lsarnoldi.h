@@ -406,7 +406,8 @@ lsa_status lsa_phiv_vjp(const lsa_op* op, const double* v, double h, int m, int 
  * groups, the rest to single CTAs, each queue taken in order of decreasing
  * cost.  group_size = lsa_batch_info's ctas with nlarge = count is one grid
  * per instance; nlarge = 0 is one CTA per instance.  lsa_batch_tune times a
- * set of tilings on the caller's data and keeps the fastest. */
+ * set of tilings on the caller's data and keeps the fastest, then (hybrid
+ * variants) the other step form on that tiling, and keeps the faster. */
 typedef struct lsa_batch lsa_batch;
 
 /* Device workspace bytes for a batch (0 if the arguments are invalid).
@@ -429,6 +430,13 @@ lsa_status lsa_batch_info(const lsa_batch* plan, int* ctas, int* group_size, int
 /* Set the tiling: 1 <= group_size <= ctas, 0 <= nlarge <= count. */
 lsa_status lsa_batch_set_tiling(lsa_batch* plan, int group_size, int nlarge);
 
+/* Step form of the hybrid variants in this plan (see lsa_tune_step): 0 the
+ * one-pass step (default), 1 the two-phase step, whose extra barrier is
+ * counted over an instance's group.  Both compute bitwise the same result.
+ * lsa_batch_step_form returns the plan's form (-1 for a null plan). */
+lsa_status lsa_batch_set_step_form(lsa_batch* plan, int two_phase);
+int lsa_batch_step_form(const lsa_batch* plan);
+
 /* Enqueue one batched evaluation on `stream` (two kernels: initialisation and
  * the persistent kernel; nothing is read back).  use_graph != 0 captures the
  * two launches once into a CUDA graph (on a private stream of the plan) and
@@ -443,9 +451,10 @@ lsa_status lsa_batch_run(lsa_batch* plan, const double* v, double* y, int use_gr
 lsa_status lsa_batch_read_stats(const lsa_batch* plan, lsa_stats* stats, int* finished, void* stream);
 
 /* Time candidate tilings (one CTA per instance, one grid per instance, and
- * groups of 2..32 CTAs for the costliest count/64 .. count/2 instances), each
+ * groups of 2..32 CTAs for the costliest count/64 .. count instances), each
  * `reps` times after one warm-up run on the caller's v and y, keep the fastest
- * and return it.  Synchronises `stream`; overwrites y. */
+ * and return it (with, for the hybrid variants, the faster step form on it,
+ * see lsa_batch_step_form).  Synchronises `stream`; overwrites y. */
 lsa_status lsa_batch_tune(lsa_batch* plan, const double* v, double* y, int reps, int* group_size,
                           int* nlarge, float* ms_best, void* stream);
 

@@ -430,6 +430,15 @@ class Batch:
         _check(B.lib().lsa_batch_set_tiling(self._h, int(group_size), int(nlarge)),
                "lsa_batch_set_tiling", ok=(B.LSA_OK,))
 
+    @property
+    def step_form(self):
+        """1 when the plan runs the two-phase hybrid step, 0 for the one-pass step."""
+        return int(B.lib().lsa_batch_step_form(self._h))
+
+    def set_step_form(self, two_phase: int):
+        _check(B.lib().lsa_batch_set_step_form(self._h, int(two_phase)), "lsa_batch_set_step_form",
+               ok=(B.LSA_OK,))
+
     def _check_v(self, v, y):
         if v.dtype != torch.float64 or not v.is_cuda or not v.is_contiguous() or v.numel() != self.v_elems:
             raise ValueError("v must be a contiguous float64 CUDA tensor of the packed size")

@@ -83,6 +83,8 @@ SIGNATURES = {
                                POINTER(c_longlong), POINTER(c_longlong), POINTER(c_longlong),
                                POINTER(c_longlong)]),
     "lsa_batch_set_tiling": (c_int, [c_void_p, c_int, c_int]),
+    "lsa_batch_set_step_form": (c_int, [c_void_p, c_int]),
+    "lsa_batch_step_form": (c_int, [c_void_p]),
     "lsa_batch_run": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
     "lsa_batch_read_stats": (c_int, [c_void_p, POINTER(LsaStats), POINTER(c_int), c_void_p]),
     "lsa_batch_tune": (c_int, [c_void_p, c_void_p, c_void_p, c_int, POINTER(c_int), POINTER(c_int),

@@ -146,6 +146,7 @@ struct lsa_batch {
   double h = 0.0, tol = 0.0;
   int G = 0;
   int gsize = 1, nlarge = 0;
+  int two_phase = 0;                 // step form of the hybrid variants
   char* w = nullptr;
   BatchLayout BL;
   std::vector<BatchInst> inst;
@@ -157,7 +158,7 @@ struct lsa_batch {
   cudaGraphExec_t gexec = nullptr;
   const double* gv = nullptr;
   double* gy = nullptr;
-  int g_gsize = 0, g_nlarge = -1;
+  int g_gsize = 0, g_nlarge = -1, g_two = -1;
 
   BatchParams params(const double* v, double* y) const {
     BatchParams BP;
@@ -167,6 +168,7 @@ struct lsa_batch {
     BP.count = count;
     BP.nlarge = nlarge;
     BP.gsize = gsize;
+    BP.two_phase = two_phase;
     BP.variant = variant;
     BP.p = p;
     BP.h = h;
@@ -203,6 +205,7 @@ struct lsa_batch {
     gv = nullptr;
     gy = nullptr;
     g_nlarge = -1;
+    g_two = -1;
   }
 
   ~lsa_batch() {
@@ -321,11 +324,20 @@ lsa_status lsa_batch_set_tiling(lsa_batch* b, int group_size, int nlarge) {
   return LSA_OK;
 }
 
+lsa_status lsa_batch_set_step_form(lsa_batch* b, int two_phase) {
+  if (!b || (two_phase != 0 && two_phase != 1)) return LSA_ERR_ARG;
+  b->two_phase = two_phase;
+  return LSA_OK;
+}
+
+int lsa_batch_step_form(const lsa_batch* b) { return b ? b->two_phase : -1; }
+
 lsa_status lsa_batch_run(lsa_batch* b, const double* v, double* y, int use_graph, void* stream) {
   if (!b || !v || !y) return LSA_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   if (!use_graph) return b->enqueue(v, y, s) == cudaSuccess ? LSA_OK : LSA_ERR_CUDA;
-  if (!(b->gexec && b->gv == v && b->gy == y && b->g_gsize == b->gsize && b->g_nlarge == b->nlarge)) {
+  if (!(b->gexec && b->gv == v && b->gy == y && b->g_gsize == b->gsize && b->g_nlarge == b->nlarge &&
+        b->g_two == b->two_phase)) {
     b->drop_graph();
     if (!b->cap && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
       b->cap = nullptr;
@@ -347,6 +359,7 @@ lsa_status lsa_batch_run(lsa_batch* b, const double* v, double* y, int use_graph
     b->gv = v;
     b->gy = y;
     b->g_gsize = b->gsize;
+    b->g_two = b->two_phase;
     b->g_nlarge = b->nlarge;
   }
   return cudaGraphLaunch(b->gexec, s) == cudaSuccess ? LSA_OK : LSA_ERR_CUDA;
@@ -410,34 +423,47 @@ lsa_status lsa_batch_tune(lsa_batch* b, const double* v, double* y, int reps, in
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return LSA_ERR_CUDA;
   if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return LSA_ERR_CUDA; }
-  const int g0 = b->gsize, nl0 = b->nlarge;
-  float best = 1e30f;
-  Cand bc = {g0, nl0};
   lsa_status result = LSA_OK;
-  for (const Cand& c : cands) {
-    b->gsize = c.g;
-    b->nlarge = c.nl;
-    if (b->enqueue(v, y, s) != cudaSuccess) { result = LSA_ERR_CUDA; break; }   // warm-up
+  // best of `reps` timed runs after one warm-up (negative: the run failed)
+  auto time_it = [&](int g, int nl, int two) -> float {
+    b->gsize = g;
+    b->nlarge = nl;
+    b->two_phase = two;
+    if (b->enqueue(v, y, s) != cudaSuccess) { result = LSA_ERR_CUDA; return -1.f; }
     float tmin = 1e30f;
     for (int r = 0; r < reps; ++r) {
       cudaEventRecord(e0, s);
-      if (b->enqueue(v, y, s) != cudaSuccess) { result = LSA_ERR_CUDA; break; }
+      if (b->enqueue(v, y, s) != cudaSuccess) { result = LSA_ERR_CUDA; return -1.f; }
       cudaEventRecord(e1, s);
-      if (cudaEventSynchronize(e1) != cudaSuccess) { result = LSA_ERR_CUDA; break; }
+      if (cudaEventSynchronize(e1) != cudaSuccess) { result = LSA_ERR_CUDA; return -1.f; }
       float t = 0.f;
       cudaEventElapsedTime(&t, e0, e1);
       tmin = t < tmin ? t : tmin;
     }
-    if (result != LSA_OK) break;
     int fin = 0;
     lsa_status st = lsa_batch_read_stats(b, nullptr, &fin, stream);
-    if (st < 0) { result = st; break; }
-    if (tmin < best) { best = tmin; bc = c; }
+    if (st < 0) { result = st; return -1.f; }
+    return tmin;
+  };
+  const int two0 = b->two_phase;
+  float best = 1e30f;
+  Cand bc = {b->gsize, b->nlarge};
+  int btwo = two0;
+  for (const Cand& c : cands) {
+    const float t = time_it(c.g, c.nl, two0);
+    if (t < 0.f) break;
+    if (t < best) { best = t; bc = c; }
+  }
+  // then the other step form of the hybrid variants on the best tiling
+  if (result == LSA_OK && is_hybrid(b->variant)) {
+    const float t = time_it(bc.g, bc.nl, 1 - two0);
+    if (t >= 0.f && t < best) { best = t; btwo = 1 - two0; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   b->gsize = bc.g;
   b->nlarge = bc.nl;
+  b->two_phase = btwo;
   if (group_size) *group_size = bc.g;
   if (nlarge) *nlarge = bc.nl;
   if (ms_best) *ms_best = best;

@@ -61,6 +61,7 @@ struct BatchParams {
   const BatchInst* inst;
   const int* order;        // group queue (nlarge entries) then single queue
   int count, nlarge, gsize;
+  int two_phase;           // hybrid variants: the two-phase step (see ArnoldiParams)
   int variant, p;
   double h, tol, brk_tol;
   long long timeout_ns;
@@ -102,7 +103,7 @@ __device__ __noinline__ bool batch_instance(const BatchParams& BP, const BatchIn
     P.m = I.m;
     P.variant = BP.variant;
     P.write_vlast = 0;
-    P.two_phase = 0;
+    P.two_phase = BP.two_phase;
     P.brk_tol = BP.brk_tol;
     P.timeout_ns = BP.timeout_ns;
     SP.H = I.H;

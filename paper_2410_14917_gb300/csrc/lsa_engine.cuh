@@ -77,6 +77,10 @@ struct Engine {
   // S.fallback_pending).  Global copies are written as in the grid kernels.
   bool cached = false;
   double* smallL = nullptr;
+  // Grid kernels running Engine::run_hybrid with the CWY or NCWY correction:
+  // every CTA keeps T in its `small` scratch, one new row per step read in
+  // load_ctl, so that whichever CTA runs the next step need not stage it.
+  bool tcache = false;
   Coef<Tc> cf;
   const int tid, lane, warp;
   int grank, gsize;                  // this CTA's rank in its group and the group size
@@ -143,6 +147,7 @@ struct Engine {
     const B* Vb = reinterpret_cast<const B*>(P.V);
     Tc* ring = S.ring + sl * NS * PS;
     const Tc a = (Tc)ps.a;
+    const bool unit = ps.a == 1.0;
     int gi[QP], so[QP];
     Tc x[QP];
 #pragma unroll
@@ -167,14 +172,16 @@ struct Engine {
         gi[u] = (int)(s * d.npts + gx + (long long)d.nx * (gy + (long long)d.ny * zw));
         so[u] = s * PS + (ly + 1) * PW + lx + 1;
         if (r < pint && own) so[u] |= (1 << 30);   // owned interior point
-        if (ps.src64) x[u] = a * (Tc)__ldg(ps.src64 + gi[u]);
-        else x[u] = a * (Tc)__ldcg(ps.srcB + gi[u]);
+        x[u] = ps.src64 ? (Tc)__ldg(ps.src64 + gi[u]) : (Tc)__ldcg(ps.srcB + gi[u]);
+        if (!unit) x[u] = a * x[u];        // (a = 1: no float64 instruction)
       }
     }
     // x -= sum_c coef_c V_c : one coefficient load per column, applied to all
     // points; loads are issued in batches of CB columns before their FMAs so
-    // that several round trips to L2/HBM overlap, and two accumulators per
-    // point halve the FMA dependency chain.
+    // that several round trips to L2/HBM overlap.  The float32 form keeps two
+    // accumulators per point (halving the FMA dependency chain); the float64
+    // form one (its pipe is throughput-bound, and the merge would be one more
+    // float64 addition per point).
     constexpr int CB = F64 ? 4 : 8;
     Tc xb[QP];
 #pragma unroll
@@ -193,7 +200,7 @@ struct Engine {
         const Tc cc = S.coefc[c + i];
 #pragma unroll
         for (int u = 0; u < QP; ++u) {
-          if (i & 1) xb[u] = fma(-cc, v[i][u], xb[u]);
+          if (!F64 && (i & 1)) xb[u] = fma(-cc, v[i][u], xb[u]);
           else x[u] = fma(-cc, v[i][u], x[u]);
         }
       }
@@ -204,8 +211,10 @@ struct Engine {
 #pragma unroll
       for (int u = 0; u < QP; ++u) x[u] = fma(-cc, (Tc)__ldcg(col + gi[u]), x[u]);
     }
+    if constexpr (!F64) {
 #pragma unroll
-    for (int u = 0; u < QP; ++u) x[u] += xb[u];
+      for (int u = 0; u < QP; ++u) x[u] += xb[u];
+    }
 #pragma unroll
     for (int u = 0; u < QP; ++u) {
       if (so[u] < 0) continue;
@@ -223,9 +232,9 @@ struct Engine {
   // CTA's contiguous share of the N values (all species; equal shares, so
   // every CTA has the same work), stored to ps.xout; no halo, no shared
   // memory, no barrier.  Each value goes through the same operations in the
-  // same order as in project_plane (CB-column batches, the two alternating
-  // accumulators, then the tail), so the stored x is bitwise the value the
-  // one-pass step stores.
+  // same order as in project_plane (CB-column batches, the float32 form's two
+  // alternating accumulators, then the tail), so the stored x is bitwise the
+  // value the one-pass step stores.
   __device__ void project_flat(const PassT<B>& ps) {
     constexpr int U = 4;                       // values per thread per round
     constexpr int CB = F64 ? 4 : 8;
@@ -236,6 +245,7 @@ struct Engine {
     const long long e1 = min(N, e0 + per);
     const B* Vb = reinterpret_cast<const B*>(P.V);
     const Tc a = (Tc)ps.a;
+    const bool unit = ps.a == 1.0;
     for (long long base = e0; base < e1; base += (long long)U * NT) {
       long long gi[U];
       Tc x[U], xb[U];
@@ -243,8 +253,8 @@ struct Engine {
       for (int u = 0; u < U; ++u) {
         const long long q = base + tid + (long long)u * NT;
         gi[u] = q < e1 ? q : e0;               // out-of-share lanes re-read a valid value
-        if (ps.src64) x[u] = a * (Tc)__ldg(ps.src64 + gi[u]);
-        else x[u] = a * (Tc)__ldcg(ps.srcB + gi[u]);
+        x[u] = ps.src64 ? (Tc)__ldg(ps.src64 + gi[u]) : (Tc)__ldcg(ps.srcB + gi[u]);
+        if (!unit) x[u] = a * x[u];
         xb[u] = (Tc)0;
       }
       int c = ps.c0;
@@ -261,7 +271,7 @@ struct Engine {
           const Tc cc = S.coefc[c + i];
 #pragma unroll
           for (int u = 0; u < U; ++u) {
-            if (i & 1) xb[u] = fma(-cc, v[i][u], xb[u]);
+            if (!F64 && (i & 1)) xb[u] = fma(-cc, v[i][u], xb[u]);
             else x[u] = fma(-cc, v[i][u], x[u]);
           }
         }
@@ -275,7 +285,7 @@ struct Engine {
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const long long q = base + tid + (long long)u * NT;
-        if (q < e1) ps.xout[q] = (B)(x[u] + xb[u]);
+        if (q < e1) ps.xout[q] = F64 ? (B)x[u] : (B)(x[u] + xb[u]);
       }
     }
   }
@@ -568,21 +578,14 @@ struct Engine {
     for (int s = tid; s < nslots; s += NT) {
       double acc = 0.0;
       int r = 0;
-      for (; r + 16 <= nrows; r += 16) {
+      for (; r < nrows; r += 16) {       // 16 loads in flight, then their sum in row order
         double v[16];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] = __ldcg(src + (long long)(r + i) * SLOTS + s);
+        for (int i = 0; i < 16; ++i) v[i] = (r + i < nrows) ? __ldcg(src + (long long)(r + i) * SLOTS + s) : 0.0;
 #pragma unroll
-        for (int i = 0; i < 16; ++i) acc += v[i];
+        for (int i = 0; i < 16; ++i)
+          if (r + i < nrows) acc += v[i];
       }
-      for (; r + 4 <= nrows; r += 4) {
-        double v[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) v[i] = __ldcg(src + (long long)(r + i) * SLOTS + s);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) acc += v[i];
-      }
-      for (; r < nrows; ++r) acc += __ldcg(src + (long long)r * SLOTS + s);
       if (to_smem) dst[s] = acc;
       else __stcg(dst + s, acc);
     }
@@ -631,11 +634,13 @@ struct Engine {
   // next pass's coefficients and flags, and the hybrid step's lazy scales,
   // norm estimate, ||A v|| and reduction count, so that whichever CTA runs
   // the next step finds them here (no L2 round trip inside the step).
-  __device__ void load_ctl(int ncoef) {
+  __device__ void load_ctl(int ncoef, int trow = -1) {
     for (int c = tid; c < ncoef; c += NT) {
       S.coefc[c] = (Tc)__ldcg(&P.ctl->coef[c]);
       S.sig[c] = __ldcg(&P.ctl->sigma[c]);
     }
+    if (tcache && trow > 0)
+      for (int k = tid; k < trow; k += NT) small[trow * MMAX + k] = __ldcg(&P.T[trow * MMAX + k]);
     if (tid == 0) {
       S.a = (Tc)__ldcg(&P.ctl->a);
       S.done = __ldcg(&P.ctl->done);
@@ -649,7 +654,7 @@ struct Engine {
 
   // Barrier + reduction; `fn` runs in the last CTA with S.red filled.
   template <class Fn>
-  __device__ bool reduce_step(unsigned& gen, int nslots, int ncoef_after, Fn fn) {
+  __device__ bool reduce_step(unsigned& gen, int nslots, int ncoef_after, Fn fn, int trow = -1) {
     const BarrierRef br = arnoldi_barrier(P.ctl);
     int r;
     if (P.gsum == nullptr || gsize > RG * RG_MAX) {
@@ -678,7 +683,7 @@ struct Engine {
       barrier_release(br, gen);
     }
     ++gen;
-    load_ctl(ncoef_after);
+    load_ctl(ncoef_after, trow);
     return true;
   }
 
@@ -773,7 +778,7 @@ struct Engine {
     } else {
       // New row of T (Alg. 5: T_{j,1:j-1} = -temp_{1:j-1,1}^T T_{1:j-1,1:j-1};
       // Alg. 6: T_{j,1:j-1} = -temp_{1:j-1,1}^T; for Alg. 7 this is M^{-1}).
-      if (!cached) stage(P.T, np);   // cached: small already holds rows 0..np-1 of T
+      if (!cached && !tcache) stage(P.T, np);   // else small already holds rows 0..np-1 of T
       if (P.variant != LSA_HNCWY) {
         // T_{j,k} = -temp1_k - sum_{i>k} temp1_i T_{i,k}: the four lanes
         // 4k..4k+3 (all eight warps) take the terms i = k+1+q, k+5+q, ...
@@ -983,6 +988,7 @@ struct Engine {
     // w_j = A x_j and the inner products.  Every value goes through the same
     // operations in the same order as in the one-pass form.
     const bool two = P.two_phase != 0 && !AUG && !cached;
+    tcache = !cached && P.variant != LSA_HGSMGS;
     for (int j = 1; j <= m; ++j) {
       PassT<B> ps;
       ps.c0 = 0; ps.c1 = j - 1;
@@ -1004,7 +1010,7 @@ struct Engine {
         ps.xout = nullptr;
       }
       int ns = run_pass(ps);
-      if (!reduce_step(gen, ns, j, [&] { hybrid_step(j); })) return;
+      if (!reduce_step(gen, ns, j, [&] { hybrid_step(j); }, j - 1)) return;
       if (S.done) return;
       if (S.fallback_pending) {
         // explicit norm of the projected vector (extra reduction of Alg. 4)

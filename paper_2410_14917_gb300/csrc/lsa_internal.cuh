@@ -237,11 +237,16 @@ struct BarrierRef {
 
 // With `arrive` false the CTA only waits for the release (it is not one of
 // the `count` participants).
+// Memory ordering: the CTA barrier orders every thread's earlier writes
+// before thread 0's fence, and thread 0's fence and atomic publish them at
+// device scope (the grid-synchronisation pattern of cooperative groups); the
+// waiting side acquires the release flag and fences before the CTA barrier
+// that lets the other threads read.
 __device__ __forceinline__ int barrier_arrive(const BarrierRef& b, unsigned gen, unsigned count,
                                               int* s_flag, long long timeout_ns, bool arrive = true) {
-  __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
+    __threadfence();
     int last = 0;
     if (arrive) {
       unsigned old = atomicAdd(b.arrive, 1u);
@@ -264,31 +269,33 @@ __device__ __forceinline__ int barrier_arrive(const BarrierRef& b, unsigned gen,
         }
       }
     }
+    __threadfence();
     *s_flag = res;
   }
   __syncthreads();
-  int r = *s_flag;
-  if (r == 1) __threadfence();
-  return r;
+  return *s_flag;
 }
 
 // Arrival at a counter that `count` CTAs reach once per generation, without
 // waiting: returns 1 in the CTA that arrived last.  Must be called by all
 // threads of the CTA.
 __device__ __forceinline__ int counter_arrive(unsigned* ctr, unsigned gen, unsigned count, int* s_flag) {
-  __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) *s_flag = (atomicAdd(ctr, 1u) == (gen + 1u) * count - 1u);
+  if (threadIdx.x == 0) {
+    __threadfence();
+    *s_flag = (atomicAdd(ctr, 1u) == (gen + 1u) * count - 1u);
+    __threadfence();
+  }
   __syncthreads();
-  int r = *s_flag;
-  if (r) __threadfence();
-  return r;
+  return *s_flag;
 }
 
 __device__ __forceinline__ void barrier_release(const BarrierRef& b, unsigned gen) {
-  __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) st_release_u32(b.release, gen + 1u);
+  if (threadIdx.x == 0) {
+    __threadfence();
+    st_release_u32(b.release, gen + 1u);
+  }
 }
 
 // Barrier of all threads of a thread-block cluster: shared and global writes

@@ -99,6 +99,27 @@ def test_batched_fp32_basis_matches_oracle():
     b.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batched_two_phase_step_bitwise_equal_and_matches_oracle(precision):
+    """The two-phase hybrid step inside the batched kernel (its extra barrier
+    counted over an instance's group, or a single CTA): bitwise the one-pass
+    result on each tiling, and within tolerance of the oracle."""
+    b, v, _ = _batch(SMALL, "hcwy", precision)
+    n = b.count
+    tol = FP64_TOL if precision == "fp64" else FP32_TOL
+    for gs, nl in [(1, 0), (4, n // 2), (8, n)]:
+        b.set_tiling(gs, nl)
+        out = []
+        for two in (0, 1):
+            b.set_step_form(two)
+            assert b.step_form == two
+            out.append(b.run(v, graph=False).clone())
+            torch.cuda.synchronize()
+        assert torch.equal(out[0], out[1]), (gs, nl)
+        _check_instances(b, out[1], SMALL, "hcwy", tol)
+    b.close()
+
+
 def test_graph_replay_is_bitwise_equal_to_direct_launch():
     b, v, _ = _batch(SMALL, "hcwy")
     b.set_tiling(4, 5)
@@ -141,7 +162,7 @@ def test_tuner_picks_a_valid_tiling_and_keeps_parity():
     b, v, _ = _batch(SMALL, "hcwy")
     gs, nl, ms = b.tune(v, reps=1)
     assert 1 <= gs <= b.ctas and 0 <= nl <= b.count and ms > 0
-    assert b.tiling == (gs, nl)
+    assert b.tiling == (gs, nl) and b.step_form in (0, 1)
     y = b.run(v, graph=True)
     torch.cuda.synchronize()
     _check_instances(b, y, SMALL, "hcwy", FP64_TOL)
