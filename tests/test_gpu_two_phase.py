@@ -139,3 +139,25 @@ def test_tune_step_records_choice():
     assert st["arnoldi_kernel"] == (0 if two else 4)
     # variants without the hybrid step: nothing to choose
     assert lsa.tune_step(op, v, cfg["m"], variant="mgs") == (0, 0.0, 0.0)
+
+
+def test_two_phase_3d_large_grid_matches_one_pass_and_oracle():
+    """The 3D ADR operator at 128^3 with m = 40 in float64 (the two-phase
+    step is the default form on 3D grids): several z-segments per tile column
+    and many flat shares per plane; both forms agree bit for bit, and the
+    two-phase phi product matches the oracle (its H-CWY form) element by
+    element."""
+    import paper_2410_14917_gb300 as lsa
+
+    cfg = W.adr3d(128, m=40, p=1)
+    op, v = _op(cfg)
+    out = {}
+    for two in (0, 1):
+        with _grid_kernel_env(two):
+            out[two] = lsa.phiv(op, v, cfg["h"], cfg["p"], cfg["m"], variant="hcwy")
+    (y0, s0), (y1, s1) = out[0], out[1]
+    assert s0["arnoldi_kernel"] == 0 and s1["arnoldi_kernel"] == 4
+    assert torch.equal(y0, y1)
+    ref, info = oracle_phiv(cfg, "hcwy")
+    assert max(rel_errors(y1, ref)) < FP64_TOL
+    assert s1["m_eff"] == info["m_eff"] == cfg["m"]
