@@ -215,7 +215,8 @@ def run_reference(args, world, rank):
     inp = W.make_inputs(cfg)
     A = OP.from_workload(cfg, inp)
     variant = args.variant
-    for _ in range(min(args.warmup, 1)):
+    n_warm = min(args.warmup, 1)       # one untimed call at most: the oracle takes seconds per call
+    for _ in range(n_warm):
         OK.phiv(lambda x: A @ x, inp["v"], cfg["h"], cfg["p"], cfg["m"], variant)
     t_steps = []
     t0 = time.perf_counter()
@@ -232,10 +233,12 @@ def run_reference(args, world, rank):
     cores = os.cpu_count()
     sample = f"{n} full phiv call(s) of {cfg['name']} (m={cfg['m']}, p={cfg['p']}, {variant})"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "phiv/s",
-            "n_gpus": world, "steps": n, "warmup": 0, "ms_per_step": 1e3 * tot / n,
+            "n_gpus": world, "steps": n, "warmup": n_warm, "ms_per_step": 1e3 * tot / n,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": cfg["name"], "m": cfg["m"], "p": cfg["p"],
-                                             "variant": variant, "precision": "fp64"},
+            "data": "synthetic", "config": {"workload": cfg["name"], "N": W.n_dof(cfg), "m": cfg["m"],
+                                             "p": cfg["p"], "h": cfg["h"], "variant": variant,
+                                             "precision": "fp64",
+                                             "parallelism": "host cores (oracle)"},
             "cpu_baseline": {"value": value, "unit": "phiv/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "phiv/s", "h2d_bytes_per_step": 0,
