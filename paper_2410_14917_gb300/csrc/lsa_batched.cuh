@@ -11,7 +11,9 @@
 // A CTA serves the group queue while that has work, then the single queue,
 // so the cheap instances fill the tail left by the expensive ones.
 // gsize = grid with nlarge = count is "the whole grid per instance" and
-// nlarge = 0 is "one CTA per instance"; the host-side tuner picks in between.
+// nlarge = 0 is "one CTA per instance"; the host-side tuner picks in between,
+// and the step form of the hybrid variants (one-pass or two-phase, whose
+// barrier between its passes is counted over the group).
 #pragma once
 
 #include "lsa_engine.cuh"

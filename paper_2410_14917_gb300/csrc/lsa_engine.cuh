@@ -4,8 +4,10 @@
 // One cooperative launch runs a whole Arnoldi process.  Each "pass" streams
 // the grid tile by tile: it projects a vector (x = a*src - sum_c coef_c V_c),
 // optionally applies the stencil (w = A x, needing the projection on a
-// one-point halo, recomputed redundantly by each tile), and accumulates inner
-// products of basis columns with x and/or w.  The per-CTA partial sums go to
+// one-point halo, recomputed redundantly by each tile -- or, in the two-phase
+// form of the hybrid step, projected once over flat shares and read back
+// after a grid barrier), and accumulates inner products of basis columns with
+// x and/or w.  The per-CTA partial sums go to
 // global memory, and one grid barrier reduces them in two levels: the last CTA
 // of each group of RG CTAs sums its group, the last group sums the group rows
 // (both in a fixed order: deterministic) and does the small O(j^2)
@@ -69,7 +71,7 @@ struct Engine {
 
   const ArnoldiParams& P;
   Smem& S;
-  double* small;                     // MMAX x MMAX scratch of the last-arriving CTA
+  double* small;                     // MMAX x MMAX scratch: T (every CTA, CWY/NCWY) or the step's staging
   // Cached mode: the same CTA runs every step (the single-cluster kernel), so T
   // (and GSMGS's L, in smallL) stay in shared memory between steps, the lazy
   // scales and scalars are read from S, and the step also leaves the next
