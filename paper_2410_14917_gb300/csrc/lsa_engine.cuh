@@ -506,16 +506,24 @@ struct Engine {
     {
       // the warp's 2*KMAX column sums at once: value 2kk is x . V_c, 2kk+1 is
       // w . V_c for column c = d0 + warp + NW*kk; lanes 2k and 2k+1 get value k
-      double v[2 * KMAX];
+      // (float32 form: the Kahan pairs reduced as compensated float32 pairs,
+      // converted to float64 once)
+      double r;
+      if constexpr (F64) {
+        double v[2 * KMAX];
 #pragma unroll
-      for (int kk = 0; kk < KMAX; ++kk) {
-        if constexpr (F64) { v[2 * kk] = ax[kk]; v[2 * kk + 1] = aw[kk]; }
-        else {
-          v[2 * kk] = (double)axs[kk] - (double)axc[kk];
-          v[2 * kk + 1] = (double)aws[kk] - (double)awc[kk];
+        for (int kk = 0; kk < KMAX; ++kk) { v[2 * kk] = ax[kk]; v[2 * kk + 1] = aw[kk]; }
+        r = warp_sum_many<2 * KMAX>(v);
+      } else {
+        float vs[2 * KMAX], ve[2 * KMAX];   // Kahan keeps sum = s - c: e = -c
+#pragma unroll
+        for (int kk = 0; kk < KMAX; ++kk) {
+          vs[2 * kk] = axs[kk]; ve[2 * kk] = -axc[kk];
+          vs[2 * kk + 1] = aws[kk]; ve[2 * kk + 1] = -awc[kk];
         }
+        warp_sum_many_comp<2 * KMAX>(vs, ve);
+        r = (double)vs[0] + (double)ve[0];
       }
-      double r = warp_sum_many<2 * KMAX>(v);
       const int k = lane >> 1, kk = k >> 1, isw = k & 1;
       const int c = ps.d0 + warp + NW * kk;
       if ((lane & 1) == 0 && c < ps.d1) {
@@ -526,14 +534,16 @@ struct Engine {
         else part[c - ps.d0] = (ps.dmode & DOT_X) ? r : 0.0;
       }
     }
-    if constexpr (!F64) {
-      sxx = (double)fxx[0] - (double)fxx[1];
-      sxw = (double)fxw[0] - (double)fxw[1];
-      sww = (double)fww[0] - (double)fww[1];
-    }
     {
-      double t[4] = {sxx, sxw, sww, 0.0};
-      const double r = warp_sum_many<4>(t);   // lane l: value l >> 3
+      double r;                              // lane l: value l >> 3
+      if constexpr (F64) {
+        double t[4] = {sxx, sxw, sww, 0.0};
+        r = warp_sum_many<4>(t);
+      } else {
+        float ts[4] = {fxx[0], fxw[0], fww[0], 0.f}, te[4] = {-fxx[1], -fxw[1], -fww[1], 0.f};
+        warp_sum_many_comp<4>(ts, te);
+        r = (double)ts[0] + (double)te[0];
+      }
       if ((lane & 7) == 0 && lane < 24) S.bred[warp][lane >> 3] = r;
     }
     __syncthreads();

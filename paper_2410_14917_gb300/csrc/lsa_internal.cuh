@@ -197,6 +197,50 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// a + b = t + err exactly in float32 arithmetic (Knuth's two-sum; no
+// multiplications, so nothing is contracted into an FMA).
+__device__ __forceinline__ float two_sum(float a, float b, float& err) {
+  const float t = a + b;
+  const float bp = t - a;
+  const float ap = t - bp;
+  err = (a - ap) + (b - bp);
+  return t;
+}
+
+// Warp sums of NV compensated float32 values (value i = s[i] + e[i]) at once,
+// with the recursive halving of warp_sum_many: every stage adds the main parts
+// with two_sum and carries the rounding error into the compensation, so the
+// sum keeps about twice float32's precision with no float64 instruction.  On
+// return lane l holds (s, e) of value l >> (5 - log2 NV) in s[0], e[0].
+template <int NV>
+__device__ __forceinline__ void warp_sum_many_comp(float (&s)[NV], float (&e)[NV]) {
+  static_assert(NV >= 1 && NV <= 32 && (NV & (NV - 1)) == 0, "NV must be a power of two <= 32");
+  const unsigned lane = threadIdx.x & 31u;
+  int d = 16;
+#pragma unroll
+  for (int h = NV / 2; h >= 1; h >>= 1, d >>= 1) {
+    const bool up = (lane & (unsigned)d) != 0u;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const float ss = up ? s[i] : s[i + h], se = up ? e[i] : e[i + h];
+      const float ks = up ? s[i + h] : s[i], ke = up ? e[i + h] : e[i];
+      const float os = __shfl_xor_sync(0xffffffffu, ss, d);
+      const float oe = __shfl_xor_sync(0xffffffffu, se, d);
+      float err;
+      s[i] = two_sum(ks, os, err);
+      e[i] = (ke + oe) + err;
+    }
+  }
+#pragma unroll
+  for (; d >= 1; d >>= 1) {
+    const float os = __shfl_xor_sync(0xffffffffu, s[0], d);
+    const float oe = __shfl_xor_sync(0xffffffffu, e[0], d);
+    float err;
+    s[0] = two_sum(s[0], os, err);
+    e[0] = (e[0] + oe) + err;
+  }
+}
+
 // Warp sums of NV per-lane values at once (NV a power of two, at most 32):
 // recursive halving, each stage trading half of the values still held with
 // the partner lane and adding the other half, so a lane does NV - 1 + (5 -
