@@ -588,25 +588,34 @@ struct StreamEngine {
     const int nd = stencil ? n : 0;
     double* part = e.P.partials + (long long)e.grank * SLOTS;
     double* wred = reinterpret_cast<double*>(stages);      // NW x 2 x MMAX (stages are idle)
+    // the eight quads of a lane group summed as compensated float32 pairs
+    // (Kahan keeps sum = s - c: the pair is (s, -c); two_sum at every stage),
+    // converted to float64 once; slots past the pass's count hold nothing
 #pragma unroll
     for (int k = 0; k < SQ_KC; ++k) {
+      if (k >= kn) break;
       const int c = g + SQ_NG * k;
-      double vx = (double)A.xs[k] - (double)A.xc[k];
-      double vw = (double)A.ws[k] - (double)A.wc[k];
+      float xs = A.xs[k], xe = -A.xc[k], ws = A.ws[k], we = -A.wc[k];
 #pragma unroll
       for (int o = 1; o < 8; o <<= 1) {
-        vx += __shfl_xor_sync(0xffffffffu, vx, o);
-        vw += __shfl_xor_sync(0xffffffffu, vw, o);
+        const float oxs = __shfl_xor_sync(0xffffffffu, xs, o), oxe = __shfl_xor_sync(0xffffffffu, xe, o);
+        const float ows = __shfl_xor_sync(0xffffffffu, ws, o), owe = __shfl_xor_sync(0xffffffffu, we, o);
+        float ex, ew;
+        xs = two_sum(xs, oxs, ex);
+        xe = (xe + oxe) + ex;
+        ws = two_sum(ws, ows, ew);
+        we = (we + owe) + ew;
       }
       if ((e.lane & 7) == 0 && c < nd) {
-        wred[(e.warp * 2) * MMAX + c] = vx;
-        wred[(e.warp * 2 + 1) * MMAX + c] = vw;
+        wred[(e.warp * 2) * MMAX + c] = (double)xs + (double)xe;
+        wred[(e.warp * 2 + 1) * MMAX + c] = (double)ws + (double)we;
       }
     }
-    double sv[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) sv[k] = warp_sum((double)A.ss[k] - (double)A.sc[k]);
-    if (e.lane == 0) { e.S.bred[e.warp][0] = sv[0]; e.S.bred[e.warp][1] = sv[1]; e.S.bred[e.warp][2] = sv[2]; }
+    {
+      float ts[4] = {A.ss[0], A.ss[1], A.ss[2], 0.f}, te[4] = {-A.sc[0], -A.sc[1], -A.sc[2], 0.f};
+      warp_sum_many_comp<4>(ts, te);           // lane l: value l >> 3
+      if ((e.lane & 7) == 0 && e.lane < 24) e.S.bred[e.warp][e.lane >> 3] = (double)ts[0] + (double)te[0];
+    }
     __syncthreads();
     for (int t = e.tid; t < 2 * nd; t += NT) {
       const int kind = t / nd, c = t - kind * nd;
