@@ -47,6 +47,22 @@ def test_phiv_parity(cfg, variant, precision):
     assert st["m_eff"] == info["m_eff"]
 
 
+@pytest.mark.parametrize("variant,precision", [("hcwy", "fp64"), ("mgs", "fp64"), ("cgs2", "fp64"),
+                                               ("hcwy", "fp32")])
+def test_phiv_grayscott512_full_size_matches_oracle(variant, precision):
+    """The Gray-Scott 512^2 workload at full size (N = 524288, m = 64, phi_0..phi_2),
+    each of its variants and the float32-basis form, against the oracle's
+    float64 MGS product element by element and normwise."""
+    cfg = W.config(1)
+    y, st, _ = run(cfg, variant, precision)
+    ref, info = oracle_phiv(cfg)
+    tol = FP64_TOL if precision == "fp64" else FP32_TOL
+    errs = rel_errors(y, ref)
+    assert max(errs) < tol, errs
+    assert st["status"] == 0 and st["m_eff"] == info["m_eff"] == cfg["m"]
+    assert st["grid_syncs"] == expected_syncs(variant, cfg["m"], st["norm_fallbacks"])
+
+
 def test_phiv_advdiff64_matches_fft_exact():
     cfg = W.config(0)
     y, st, inp = run(cfg, "hcwy", "fp64")
