@@ -161,3 +161,20 @@ def test_two_phase_3d_large_grid_matches_one_pass_and_oracle():
     ref, info = oracle_phiv(cfg, "hcwy")
     assert max(rel_errors(y1, ref)) < FP64_TOL
     assert s1["m_eff"] == info["m_eff"] == cfg["m"]
+
+
+def test_two_phase_adr256_full_size_matches_oracle():
+    """The 3D ADR 256^3 workload (N = 16.7M, m = 40) in float64, where the
+    two-phase step is the default form: the phi product against the oracle's
+    H-CWY form (the same oracle product the streaming float32 test compares
+    with; the oracle's pins hold H-CWY equal to MGS) element by element."""
+    import paper_2410_14917_gb300 as lsa
+
+    cfg = W.config(2)
+    op, v = _op(cfg)
+    with _grid_kernel_env(1):
+        y, st = lsa.phiv(op, v, cfg["h"], cfg["p"], cfg["m"], variant="hcwy")
+    assert st["arnoldi_kernel"] == 4 and st["status"] == 0
+    ref, info = oracle_phiv(cfg, "hcwy")
+    assert max(rel_errors(y, ref)) < FP64_TOL
+    assert st["m_eff"] == info["m_eff"] == cfg["m"]
