@@ -42,6 +42,30 @@ __device__ __forceinline__ double hhat(const SmallParams& P, int m, double scale
   return v * scale;
 }
 
+// sum_k A[r][k] B[k][c] over k < n (leading dimension LD): eight loads of each
+// operand in flight per round trip to L2 (a product entry is one thread's
+// chain, so its loads, not its FMAs, set the time), four accumulators
+// combined in a fixed order.
+__device__ __forceinline__ double dot_rc(const double* A, const double* B, int r, int c, int n) {
+  const double* a = A + r * LD;
+  const double* b = B + c;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  for (int k = 0; k < n; k += 8) {
+    double x[8], y[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const bool in = k + i < n;
+      x[i] = in ? __ldcg(a + k + i) : 0.0;
+      y[i] = in ? __ldcg(b + (k + i) * LD) : 0.0;
+    }
+    s0 = fma(x[0], y[0], s0); s1 = fma(x[1], y[1], s1);
+    s2 = fma(x[2], y[2], s2); s3 = fma(x[3], y[3], s3);
+    s0 = fma(x[4], y[4], s0); s1 = fma(x[5], y[5], s1);
+    s2 = fma(x[6], y[6], s2); s3 = fma(x[7], y[7], s3);
+  }
+  return (s0 + s1) + (s2 + s3);
+}
+
 // B_l = sum_{i=0}^{3} a_{4l+i} X^i  (a_k = 1/k!; B_4 = a16 I + a17 X + a18 X^2)
 __device__ __forceinline__ double block_coef(const double* X, const double* X2, const double* X3,
                                              int l, int r, int c, const double* a) {
@@ -162,14 +186,7 @@ static __device__ __noinline__ bool expm_group(const SmallParams& P, int grank, 
   // X2 = X X
   for (int o = gtid; o < nn; o += gstride) {
     int r = o / n, c = o - r * n;
-    double s0 = 0.0, s1 = 0.0;
-    int k = 0;
-    for (; k + 1 < n; k += 2) {
-      s0 = fma(__ldcg(X + r * LD + k), __ldcg(X + k * LD + c), s0);
-      s1 = fma(__ldcg(X + r * LD + k + 1), __ldcg(X + (k + 1) * LD + c), s1);
-    }
-    if (k < n) s0 = fma(__ldcg(X + r * LD + k), __ldcg(X + k * LD + c), s0);
-    X2[r * LD + c] = s0 + s1;
+    X2[r * LD + c] = dot_rc(X, X, r, c, n);
   }
   EXPM_BARRIER();
   // X3 = X2 X, X4 = X2 X2
@@ -177,15 +194,7 @@ static __device__ __noinline__ bool expm_group(const SmallParams& P, int grank, 
     int which = o >= nn;
     int oo = o - which * nn;
     int r = oo / n, c = oo - r * n;
-    const double* Bm = which ? X2 : X;
-    double s0 = 0.0, s1 = 0.0;
-    int k = 0;
-    for (; k + 1 < n; k += 2) {
-      s0 = fma(__ldcg(X2 + r * LD + k), __ldcg(Bm + k * LD + c), s0);
-      s1 = fma(__ldcg(X2 + r * LD + k + 1), __ldcg(Bm + (k + 1) * LD + c), s1);
-    }
-    if (k < n) s0 = fma(__ldcg(X2 + r * LD + k), __ldcg(Bm + k * LD + c), s0);
-    (which ? X4 : X3)[r * LD + c] = s0 + s1;
+    (which ? X4 : X3)[r * LD + c] = dot_rc(X2, which ? X2 : X, r, c, n);
   }
   EXPM_BARRIER();
   // Horner in X^4: R = B_4; R = B_l + X^4 R for l = 3, 2, 1, 0
@@ -194,13 +203,27 @@ static __device__ __noinline__ bool expm_group(const SmallParams& P, int grank, 
   for (int l = 3; l >= 0; --l) {
     for (int o = gtid; o < nn; o += gstride) {
       int r = o / n, c = o - r * n;
-      double s0 = 0.0, s1 = 0.0;
-      for (int k = 0; k < n; ++k) {
-        double rk = (l == 3) ? block_coef(X, X2, X3, 4, k, c, a) : __ldcg(Rin + k * LD + c);
-        if (k & 1) s1 = fma(__ldcg(X4 + r * LD + k), rk, s1);
-        else s0 = fma(__ldcg(X4 + r * LD + k), rk, s0);
+      double acc;
+      if (l < 3) {
+        acc = dot_rc(X4, Rin, r, c, n);
+      } else {                           // R = B_4 formed on the fly: eight of its entries per round trip
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        for (int k = 0; k < n; k += 8) {
+          double x[8], y[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const bool in = k + i < n;
+            x[i] = in ? __ldcg(X4 + r * LD + k + i) : 0.0;
+            y[i] = in ? block_coef(X, X2, X3, 4, k + i, c, a) : 0.0;
+          }
+          s0 = fma(x[0], y[0], s0); s1 = fma(x[1], y[1], s1);
+          s2 = fma(x[2], y[2], s2); s3 = fma(x[3], y[3], s3);
+          s0 = fma(x[4], y[4], s0); s1 = fma(x[5], y[5], s1);
+          s2 = fma(x[6], y[6], s2); s3 = fma(x[7], y[7], s3);
+        }
+        acc = (s0 + s1) + (s2 + s3);
       }
-      Rout[r * LD + c] = block_coef(X, X2, X3, l, r, c, a) + (s0 + s1);
+      Rout[r * LD + c] = block_coef(X, X2, X3, l, r, c, a) + acc;
     }
     EXPM_BARRIER();
     double* t = Rin; Rin = Rout; Rout = t;
@@ -209,14 +232,7 @@ static __device__ __noinline__ bool expm_group(const SmallParams& P, int grank, 
   for (int q = 0; q < s; ++q) {
     for (int o = gtid; o < nn; o += gstride) {
       int r = o / n, c = o - r * n;
-      double s0 = 0.0, s1 = 0.0;
-      int k = 0;
-      for (; k + 1 < n; k += 2) {
-        s0 = fma(__ldcg(Rin + r * LD + k), __ldcg(Rin + k * LD + c), s0);
-        s1 = fma(__ldcg(Rin + r * LD + k + 1), __ldcg(Rin + (k + 1) * LD + c), s1);
-      }
-      if (k < n) s0 = fma(__ldcg(Rin + r * LD + k), __ldcg(Rin + k * LD + c), s0);
-      Rout[r * LD + c] = s0 + s1;
+      Rout[r * LD + c] = dot_rc(Rin, Rin, r, c, n);
     }
     EXPM_BARRIER();
     double* t = Rin; Rin = Rout; Rout = t;
