@@ -72,6 +72,12 @@ cudaError_t launch_expm(const SmallParams& P, cudaStream_t s) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_expm, EXPM_NT, 0);
   int G = sms * (nb > 0 ? (nb < 2 ? nb : 2) : 1);
+  // one product entry per thread in the largest phase (X^3 and X^4 together,
+  // 2 n^2 entries for n = m + p + 1 at most): more CTAs would only wait at the
+  // barrier between the products
+  const int n = P.m + P.p + 1;
+  const int need = (2 * n * n + EXPM_NT - 1) / EXPM_NT;
+  if (need < G) G = need > 0 ? need : 1;
   SmallParams Pc = P;
   void* args[1] = {&Pc};
   return cudaLaunchCooperativeKernel((void*)k_expm, dim3(G), dim3(EXPM_NT), args, 0, s);
