@@ -431,8 +431,9 @@ lsa_status lsa_batch_info(const lsa_batch* plan, int* ctas, int* group_size, int
 lsa_status lsa_batch_set_tiling(lsa_batch* plan, int group_size, int nlarge);
 
 /* Step form of the hybrid variants in this plan (see lsa_tune_step): 0 the
- * one-pass step (default), 1 the two-phase step, whose extra barrier is
- * counted over an instance's group.  Both compute bitwise the same result.
+ * one-pass step, 1 the two-phase step (the default for the hybrid variants;
+ * its extra barrier is counted over an instance's group).  Both compute
+ * bitwise the same result.
  * lsa_batch_step_form returns the plan's form (-1 for a null plan). */
 lsa_status lsa_batch_set_step_form(lsa_batch* plan, int two_phase);
 int lsa_batch_step_form(const lsa_batch* plan);

@@ -238,3 +238,16 @@ def test_full_workload_sampled_against_oracle():
                         + [int(x) for x in rng.choice(len(insts), 3, replace=False)]))
     _check_instances(b, y, bcfg, "hcwy", FP64_TOL, idx=sample)
     b.close()
+
+
+@pytest.mark.parametrize("variant", ["hcwy", "mgs"])
+def test_batched_default_step_form(variant):
+    """A new plan runs the two-phase step for the hybrid variants (the one
+    that the tuner picks on the benchmark batch) and the one-pass passes of
+    the other variants."""
+    b, v, _ = _batch(SMALL, variant)
+    assert b.step_form == (1 if variant == "hcwy" else 0)
+    y = b.run(v, graph=False)
+    torch.cuda.synchronize()
+    _check_instances(b, y, SMALL, variant, FP64_TOL)
+    b.close()
