@@ -44,7 +44,8 @@ FALLBACK_HBM_GBS = 6800.0
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) of one launch of the dominant kernel from an ncu
 # capture of the current kernel, keyed by workload, precision, variant and
-# Arnoldi kernel kind (0 one-pass, 4 two-phase grid kernel, 2 streaming);
+# Arnoldi kernel kind (0 one-pass, 4 two-phase grid kernel, 5 flat two-phase
+# kernel, 2 streaming);
 # a workload without an up-to-date capture reports null.  Gray-Scott 512^2:
 # profiles/k_arnoldi_grayscott2d_512_fp64.md (both step forms); the 3D line's
 # capture is of the 192^3 case (same tiling), scaled by the unknowns
@@ -830,6 +831,7 @@ def phiv_roofline(cfg, precision, variant, ms_a, m_eff, kernel_kind, fp64_peak, 
                            "exponential and the output combination fused into the launch)"
                            if kernel_kind == 3 else
                            "k_arnoldi (persistent hybrid Arnoldi, two-phase step)" if kernel_kind == 4 else
+                           "k_arnoldi_flat (persistent hybrid Arnoldi, flat two-phase step)" if kernel_kind == 5 else
                            "k_arnoldi (persistent hybrid Arnoldi, one-pass step)"),
                 "peak_source": fp64_peak_src,
                 "hbm_gbs": byts / (ms_a / 1e3) / 1e9, "hbm_frac": byts / (ms_a / 1e3) / 1e9 / hbm_peak,
@@ -838,7 +840,8 @@ def phiv_roofline(cfg, precision, variant, ms_a, m_eff, kernel_kind, fp64_peak, 
     return {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
             "frac": achieved / hbm_peak,
             "traffic": PROFILED_TRAFFIC.get((cfg["name"], precision, variant, kernel_kind)),
-            "kernel": {0: "k_arnoldi", 1: "k_arnoldi_tma", 2: "k_arnoldi_stream", 4: "k_arnoldi"}[kernel_kind]
+            "kernel": {0: "k_arnoldi", 1: "k_arnoldi_tma", 2: "k_arnoldi_stream", 4: "k_arnoldi",
+                       5: "k_arnoldi_flat"}[kernel_kind]
                       + " (persistent Arnoldi, float32 basis)",
             "peak_source": f"{peak_kind} hbm_gbs",
             "algorithmic_bytes": byts, "algorithmic_flops": flops}
@@ -885,7 +888,7 @@ def time_phiv(lsa, torch, cfg, precision, variant, steps, warmup, dev, flush, st
     torch.cuda.synchronize()
     step_form = None
     if ms_one > 0:
-        step_form = {"chosen": "two-phase" if two else "one-pass", "tuner_ms_one_pass": ms_one,
+        step_form = {"chosen": ["one-pass", "two-phase", "flat two-phase"][two], "tuner_ms_one_pass": ms_one,
                      "tuner_ms_two_phase": ms_two}
     return dict(step_ms=[a.elapsed_time(b) for a, b in ev], k_arn=k_arn, k_exp=k_exp, k_cmb=k_cmb, st0=st0,
                 op=op, v=v, v_host=v_host, y=y, work=work, inp=inp, N=N, launches=launches,

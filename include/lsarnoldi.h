@@ -117,8 +117,9 @@ typedef struct {
   int launches;           /* kernels this call launched */
   int arnoldi_kernel;     /* Arnoldi kernel that ran: 0 plain loads, 1 TMA-staged tile+halo,
                              2 streaming (interior-only TMA stages), 3 single thread-block
-                             cluster, 4 plain loads with the two-phase step (see
-                             lsa_tune_step); filled by lsa_arnoldi/lsa_phiv */
+                             cluster, 4 plain loads with the two-phase step, 5 the flat
+                             two-phase step (see lsa_tune_step); filled by
+                             lsa_arnoldi/lsa_phiv */
 } lsa_stats;
 
 /* Largest supported Krylov dimension m. */
@@ -161,28 +162,33 @@ lsa_status lsa_arnoldi(const lsa_op* op, const double* v, int m, int variant, in
                        lsa_stats* stats, void* stream);
 
 /* Step form of the grid Arnoldi kernel's hybrid variants (Alg. 4 with
- * Algs. 5/6/7).  The one-pass form projects each tile together with its
+ * Algs. 5/6/7).  Form 0, one pass: each tile is projected together with its
  * one-point halo (the halo values are projected again by the neighbouring
- * tile), applies the stencil and forms the inner products, then reduces: one
- * grid barrier per step.  The two-phase form projects every value once, waits
- * at a grid barrier without a reduction, then reads the projected vector back
- * with its halo for the stencil and the inner products: no repeated
- * projection work, one more barrier per step.  Both compute bitwise the same
- * basis and H.
- * lsa_tune_step times both forms of lsa_arnoldi's Arnoldi kernel on
- * (op, m, variant, precision) and records the faster one; later lsa_arnoldi,
+ * tile), then the stencil and the inner products, then the reduction: one
+ * grid barrier per step.  Form 1, two-phase: every value is projected once
+ * (equal flat shares per CTA), a grid barrier without a reduction, then a
+ * pass over tiles reads the projected vector back with its halo for the
+ * stencil and the inner products: no repeated projection, one more barrier
+ * per step; bitwise the basis and H of form 0.  Form 2, flat two-phase (the
+ * 3D ADR operator): the second pass also runs over the equal flat shares,
+ * reading the stencil's neighbours through L2, with no tiles; the same
+ * stencil values, inner products summed over other groups of points (equal
+ * to forms 0 and 1 to rounding).
+ * lsa_tune_step times the forms of lsa_arnoldi's Arnoldi kernel that apply
+ * on (op, m, variant, precision) and records the fastest; later lsa_arnoldi,
  * lsa_phiv and lsa_phiv_host calls on the current device with the same
  * operator kind and grid, m, variant and precision use it (process-wide
- * table, thread-safe).  LSA_TWO_PHASE=0 or 1 in the environment overrides the
- * table.  Without either, the two-phase form runs on 3D grids and on float64
- * 2D grids of at least six 16 x 16 tiles per SM, the one-pass form otherwise
- * (the crossover measured on GB300).
+ * table, thread-safe).  LSA_TWO_PHASE=0, 1 or 2 in the environment overrides
+ * the table (2 runs form 1 where form 2 does not apply).  Without either:
+ * form 2 for float64 3D grids, form 1 for float32-basis 3D grids and for
+ * float64 2D grids of at least six 16 x 16 tiles per SM, form 0 otherwise
+ * (the crossovers measured on GB300).
  *  v      dev, N doubles: start vector of the timing runs (not modified).
  *  work   dev workspace of lsa_workspace_bytes(op, m, 0, precision).
  *  reps   timed runs per form (>= 1; one untimed run precedes them).
- *  two_phase  out (may be NULL): 1 if the two-phase form was recorded.
- *  ms_one, ms_two  out (may be NULL): best Arnoldi kernel time of each form
- *         in ms.
+ *  two_phase  out (may be NULL): the recorded form (0, 1 or 2).
+ *  ms_one, ms_two  out (may be NULL): best Arnoldi kernel time of form 0 and
+ *         of the fastest two-phase form, in ms.
  * When the forms do not apply (the variant is not hybrid, or the call would
  * run the TMA, streaming or cluster kernel) nothing is timed or recorded and
  * the outputs are 0.  Synchronises the stream. */

@@ -212,10 +212,12 @@ def phiv_host(op: Operator, v_host: torch.Tensor, h: float, p: int, m: int, y_ho
 
 def tune_step(op: Operator, v: torch.Tensor, m: int, variant="hcwy", precision="fp64", reps: int = 3,
               work=None, stream=None):
-    """Times the one-pass and the two-phase hybrid step of the grid Arnoldi
-    kernel on (op, m, variant, precision) (lsa_tune_step) and records the
-    faster form for later calls with that shape.  Returns (two_phase, ms_one,
-    ms_two); (0, 0.0, 0.0) when the forms do not apply."""
+    """Times the step forms of the grid Arnoldi kernel's hybrid variants (0
+    one-pass; 1 two-phase, its second pass over tiles; 2 flat two-phase, on
+    the 3D ADR operator) on (op, m, variant, precision) (lsa_tune_step) and
+    records the fastest for later calls with that shape.  Returns (form, ms of
+    form 0, ms of the fastest two-phase form); (0, 0.0, 0.0) when the forms do
+    not apply."""
     if v.dtype != torch.float64 or not v.is_cuda or not v.is_contiguous() or v.numel() != op.N:
         raise ValueError("v must be a contiguous float64 CUDA tensor of N values")
     m = min(int(m), op.N)

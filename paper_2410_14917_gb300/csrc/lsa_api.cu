@@ -20,6 +20,7 @@ cudaError_t launch_matvec_adr3d(const ArnoldiParams&, int, const void*, void*, i
 int blocks_per_sm_advdiff2d(int);
 int blocks_per_sm_grayscott2d(int);
 int blocks_per_sm_adr3d(int);
+int flat_blocks_per_sm_adr3d(int);
 bool tma_applicable_advdiff2d(const DevOp&, const Tiling&, int, int);
 bool tma_applicable_grayscott2d(const DevOp&, const Tiling&, int, int);
 bool tma_applicable_adr3d(const DevOp&, const Tiling&, int, int);
@@ -200,14 +201,21 @@ static bool use_cluster(const ArnoldiParams& P, int precision) {
   return c > 0;
 }
 
-// Two-phase step of the grid kernel's hybrid variants (project; grid
-// barrier; stencil and inner products: no halo projection, one more barrier
-// per step).  Chosen per device, operator shape, m, variant and precision:
-// LSA_TWO_PHASE=0/1 in the environment forces it; otherwise the form that
+// Step form of the grid kernel's hybrid variants: 0 one pass; 1 two-phase
+// (project over flat shares; grid barrier; stencil and inner products over
+// tiles: no halo projection, one more barrier per step); 2 flat two-phase (3D
+// grids of one species: the second pass also over flat shares, the stencil's
+// neighbours read through L2, no tile chain; its own kernel).  Chosen per
+// device, operator shape, m, variant and precision:
+// LSA_TWO_PHASE=0/1/2 in the environment forces it (2 runs form 1 where the
+// flat kernel does not exist); otherwise the form that
 // lsa_tune_step recorded for the shape; otherwise a default measured on
-// GB300: two-phase for 3D grids (the z-halo planes make the repeated
-// projection large) and for float64 2D grids with at least six 16x16 tiles
-// per SM, one-pass below that (the extra barrier costs more than the halo).
+// GB300: a two-phase form for 3D grids (the z-halo planes make the repeated
+// projection large): the flat one in float64 (ADR 256^3: 93 against 119 ms),
+// the tile one for the float32 basis (where it is used at all: the streaming
+// kernel runs those grids first); two-phase for float64 2D grids with at
+// least six 16x16 tiles per SM, one-pass below that (the extra barrier costs
+// more than the halo).
 struct StepKey {
   int dev, kind, nx, ny, nz, m, variant, precision;
   bool operator<(const StepKey& o) const {
@@ -238,7 +246,7 @@ static int two_phase_choice(const ArnoldiParams& P, int precision) {
   if (!two_phase_applies(P, precision)) return 0;
   if (g_step_force >= 0) return g_step_force;
   const char* env = getenv("LSA_TWO_PHASE");
-  if (env && (env[0] == '0' || env[0] == '1')) return env[0] - '0';
+  if (env && env[0] >= '0' && env[0] <= '2') return env[0] - '0';
   StepKey k;
   if (!step_key(P, precision, &k)) return 0;
   {
@@ -246,24 +254,46 @@ static int two_phase_choice(const ArnoldiParams& P, int precision) {
     auto it = g_step_choice.find(k);
     if (it != g_step_choice.end()) return it->second;
   }
-  if (P.op.nz > 1) return 1;
+  if (P.op.nz > 1) return precision == LSA_FP64 ? 2 : 1;
   return (precision == LSA_FP64 && P.tl.ntiles >= 6 * sm_count()) ? 1 : 0;
+}
+
+// The flat two-phase kernel exists for the 3D ADR operator, and its grid must
+// be resident: as many CTAs per SM as the grid kernel's layout assumes.
+static bool flat_fits(const ArnoldiParams& P, int precision) {
+  if (P.op.kind != LSA_OP_ADR3D) return false;
+  static int cache[2][16];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 16) dev = 0;
+  int& c = cache[precision][dev];
+  if (c == 0) c = flat_blocks_per_sm_adr3d(precision) >= arnoldi_blocks_per_sm(P.op, precision) ? 1 : -1;
+  return c > 0;
+}
+
+static int step_form(const ArnoldiParams& P, int precision) {
+  const int form = two_phase_choice(P, precision);
+  return (form == 2 && !flat_fits(P, precision)) ? 1 : form;
 }
 
 static int arnoldi_kernel_kind(const ArnoldiParams& P, int precision) {
   if (use_cluster(P, precision)) return 3;
   if (use_stream(P, precision)) return 2;
   if (use_tma(P, precision)) return 1;
-  return two_phase_choice(P, precision) ? 4 : 0;
+  const int form = step_form(P, precision);
+  return form == 0 ? 0 : 3 + form;
 }
 
 static cudaError_t launch_arnoldi_grid(const ArnoldiParams& P, int precision, int G, cudaStream_t s);
 
 cudaError_t launch_arnoldi(const ArnoldiParams& P, int precision, int G, cudaStream_t s) {
-  if (P.two_phase == 0 && two_phase_choice(P, precision)) {
-    ArnoldiParams Q = P;
-    Q.two_phase = 1;
-    return launch_arnoldi_grid(Q, precision, G, s);
+  if (P.two_phase == 0) {
+    const int form = step_form(P, precision);
+    if (form) {
+      ArnoldiParams Q = P;
+      Q.two_phase = form;
+      return launch_arnoldi_grid(Q, precision, G, s);
+    }
   }
   return launch_arnoldi_grid(P, precision, G, s);
 }
@@ -613,9 +643,10 @@ lsa_status lsa_tune_step(const lsa_op* op, const double* v, int m, int variant, 
     cudaEventDestroy(e0);
     return LSA_ERR_CUDA;
   }
-  float best[2] = {1e30f, 1e30f};
+  const int nforms = flat_fits(P, precision) ? 3 : 2;
+  float best[3] = {1e30f, 1e30f, 1e30f};
   lsa_status result = LSA_OK;
-  for (int form = 0; form < 2 && result == LSA_OK; ++form) {
+  for (int form = 0; form < nforms && result == LSA_OK; ++form) {
     g_step_force = form;
     for (int r = 0; r <= reps; ++r) {           // r = 0: warm-up
       cudaError_t e = launch_init(P.ctl, pr.d, (float*)pr.d.g0, (float*)pr.d.g1, precision, P.H,
@@ -643,14 +674,16 @@ lsa_status lsa_tune_step(const lsa_op* op, const double* v, int m, int variant, 
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (result != LSA_OK) return result;
-  const int choice = best[1] < best[0] ? 1 : 0;
+  int choice = 0;
+  for (int form = 1; form < nforms; ++form)
+    if (best[form] < best[choice]) choice = form;
   {
     std::lock_guard<std::mutex> lock(g_step_mu);
     g_step_choice[key] = choice;
   }
   if (two_phase) *two_phase = choice;
   if (ms_one) *ms_one = best[0];
-  if (ms_two) *ms_two = best[1];
+  if (ms_two) *ms_two = best[1] < best[2] ? best[1] : best[2];
   return LSA_OK;
 }
 

@@ -14,6 +14,7 @@ cudaError_t launch_matvec_adr3d(const ArnoldiParams& P, int precision, const voi
   return launch_matvec_op<OpADR3D>(P, precision, x, y, G, s);
 }
 int blocks_per_sm_adr3d(int precision) { return blocks_per_sm_op<OpADR3D>(precision); }
+int flat_blocks_per_sm_adr3d(int precision) { return flat_blocks_per_sm_op<OpADR3D>(precision); }
 bool tma_applicable_adr3d(const DevOp& d, const Tiling& tl, int m, int precision) {
   return precision == LSA_FP32_BASIS ? tma_applicable_op<OpADR3D, float>(d, tl, m)
                                      : tma_applicable_op<OpADR3D, double>(d, tl, m);

@@ -292,6 +292,126 @@ struct Engine {
     }
   }
 
+  // Second pass of the flat two-phase step (3D grids of one species): this
+  // CTA's equal flat share (the first pass's share) in chunks of FCH points.
+  // Each thread forms w = A x at FQ points with the seven neighbours of x read
+  // through L2 (x was stored by the first pass, before the grid barrier; the
+  // grid is periodic in every direction, as in the tile passes), stores w and
+  // adds the self terms; then the warps form the inner products with basis
+  // columns (warp <-> columns, lane <-> points, as in dots_plane) from the
+  // chunk's x and w in shared memory (xs, ws: FCH values each).  No halo copy,
+  // no tile chain: every CTA has the same number of points.  w is bitwise the
+  // tile passes' value (same operator arithmetic); the inner products sum the
+  // points in other groups, so they agree with the tile passes to rounding.
+  static constexpr int FQ = 2, FCH = FQ * NT;
+  __device__ int run_pass_flat(const PassT<B>& ps, Tc* xs, Tc* ws) {
+    static_assert(NS == 1 && DIM == 3, "the flat pass is written for 3D grids of one species");
+    const DevOp& d = P.op;
+    const long long N = d.N;
+    long long per = (N + gsize - 1) / gsize;
+    per = (per + 31) & ~31LL;                  // the shares of project_flat
+    const long long e0 = (long long)grank * per;
+    const long long e1 = min(N, e0 + per);
+    const B* xg = ps.srcB;
+    const int nxy = d.nx * d.ny;
+    const bool dx = ps.dmode & DOT_X, dw = ps.dmode & DOT_W;
+    zero_acc();
+    for (long long base = e0; base < e1; base += FCH) {
+#pragma unroll
+      for (int u = 0; u < FQ; ++u) {
+        const int pl = tid + u * NT;
+        Tc xv = (Tc)0, wv = (Tc)0;
+        if (base + pl < e1) {
+          // grid indices in 32 bits, as in the tile passes (N < 2^31)
+          const int q = (int)base + pl;
+          const int r = q / d.nx, ix = q - r * d.nx;
+          const int iz = r / d.ny, iy = r - iz * d.ny;
+          // plane values in the layout Op::apply_f reads with a row pitch of 2:
+          // [south, west, centre, east, north]; below and above at index 2
+          Tc c5[5], zm[3], zp[3];
+          c5[2] = (Tc)__ldcg(xg + q);
+          c5[1] = (Tc)__ldcg(xg + (ix == 0 ? q + (d.nx - 1) : q - 1));
+          c5[3] = (Tc)__ldcg(xg + (ix == d.nx - 1 ? q - (d.nx - 1) : q + 1));
+          c5[0] = (Tc)__ldcg(xg + (iy == 0 ? q + (d.ny - 1) * d.nx : q - d.nx));
+          c5[4] = (Tc)__ldcg(xg + (iy == d.ny - 1 ? q - (d.ny - 1) * d.nx : q + d.nx));
+          zm[2] = (Tc)__ldcg(xg + (iz == 0 ? q + (d.nz - 1) * nxy : q - nxy));
+          zp[2] = (Tc)__ldcg(xg + (iz == d.nz - 1 ? q - (d.nz - 1) * nxy : q + nxy));
+          zm[0] = zm[1] = zp[0] = zp[1] = (Tc)0;
+          Tc rr;
+          if constexpr (F64) rr = (Tc)__ldg(d.f0 + q);
+          else rr = (Tc)__ldg(d.g0 + q);
+          Tc out[1];
+          Op::template apply_f<Tc, 2>(cf, zm, c5, zp, 2, rr, (Tc)0, out);
+          xv = c5[2];
+          wv = out[0];
+          if constexpr (!F64) wv = (Tc)(B)wv;
+          ps.wout[q] = (B)wv;
+          if (ps.self & SELF_XX) self_add(0, xv, xv);
+          if (ps.self & SELF_XW) self_add(1, xv, wv);
+          if (ps.self & SELF_WW) self_add(2, wv, wv);
+        }
+        xs[pl] = xv;
+        ws[pl] = wv;
+      }
+      __syncthreads();
+      if (ps.d1 > ps.d0) {
+        // lane l takes points l + 32k of the chunk, k < FCH/32, in groups of 8;
+        // CK columns' loads in flight together (two spill registers in the
+        // float32 kernel, so one)
+        constexpr int NPL = FCH / 32;
+        constexpr int CK = 1;
+        const int nv = (int)min((long long)FCH, e1 - base);   // valid points of the chunk
+#pragma unroll
+        for (int kk = 0; kk < KMAX; kk += CK) {
+          if (ps.d0 + warp + NW * kk >= ps.d1) break;
+          Tc v[CK][NPL];
+#pragma unroll
+          for (int i = 0; i < CK; ++i) {
+            const int c = ps.d0 + warp + NW * (kk + i);
+            if (c < ps.d1) {
+              const B* col = Vc(c) + base;
+#pragma unroll
+              for (int k = 0; k < NPL; ++k) {
+                const int pl = lane + 32 * k;
+                v[i][k] = (Tc)__ldcg(col + (pl < nv ? pl : 0));   // beyond the share: x = w = 0 there
+              }
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < CK; ++i) {
+            if (ps.d0 + warp + NW * (kk + i) >= ps.d1) break;
+#pragma unroll
+            for (int g = 0; g < NPL / 8; ++g) {
+              if constexpr (F64) {
+                double a = ax[kk + i], b = aw[kk + i];
+#pragma unroll
+                for (int k = 8 * g; k < 8 * g + 8; ++k) {
+                  const int pl = lane + 32 * k;
+                  if (dx) a = fma((double)v[i][k], (double)xs[pl], a);
+                  if (dw) b = fma((double)v[i][k], (double)ws[pl], b);
+                }
+                ax[kk + i] = a;
+                aw[kk + i] = b;
+              } else {
+                float px = 0.f, pw = 0.f;
+#pragma unroll
+                for (int k = 8 * g; k < 8 * g + 8; ++k) {
+                  const int pl = lane + 32 * k;
+                  px = fmaf((float)v[i][k], (float)xs[pl], px);
+                  pw = fmaf((float)v[i][k], (float)ws[pl], pw);
+                }
+                if (dx) kahan(axs[kk + i], axc[kk + i], px);
+                if (dw) kahan(aws[kk + i], awc[kk + i], pw);
+              }
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+    return write_partials(ps);
+  }
+
   // Stencil at plane z (interior only) from the ring: w = A x.
   __device__ void stencil_plane(const PassT<B>& ps, int x0, int y0, int z, int w, int hg) {
     const DevOp& d = P.op;
@@ -987,7 +1107,11 @@ struct Engine {
   // x_j = u_j / nrm_est_{j-1} (u_j the projected vector); the normalised
   // v_j = sigma_j x_j with sigma_j = 1/||x_j|| known after step j.  All the
   // rescalings of Alg. 4 are folded into the scalars a, coef and sigma.
-  __device__ void run_hybrid() {
+  // kFlat: the instantiation of k_arnoldi_flat (3D grids of one species),
+  // whose two-phase step runs run_pass_flat after the flat projection (fbuf:
+  // 2*FCH values of shared memory); the other kernels carry none of its code.
+  template <bool kFlat = false>
+  __device__ void run_hybrid(Tc* fbuf = nullptr) {
     B* V = reinterpret_cast<B*>(P.V);
     B* Wb[2] = {reinterpret_cast<B*>(P.W0), reinterpret_cast<B*>(P.W1)};
     const long long N = P.op.N;
@@ -1021,7 +1145,9 @@ struct Engine {
         ps.srcB = ps.xout;
         ps.xout = nullptr;
       }
-      int ns = run_pass(ps);
+      int ns;
+      if constexpr (kFlat) ns = two ? run_pass_flat(ps, fbuf, fbuf + FCH) : run_pass(ps);
+      else ns = run_pass(ps);
       if (!reduce_step(gen, ns, j, [&] { hybrid_step(j); }, j - 1)) return;
       if (S.done) return;
       if (S.fallback_pending) {
@@ -1265,6 +1391,24 @@ __global__ void __launch_bounds__(NT, (sizeof(Tc) == 8) ? LSA_MINB_F64 : LSA_MIN
   else e.run_hybrid();
 }
 
+// The hybrid variants with the flat two-phase step (3D grids of one species):
+// a separate instantiation with 2*FCH values of extra shared memory.
+template <class Op, class Tc>
+__global__ void __launch_bounds__(NT, (sizeof(Tc) == 8) ? LSA_MINB_F64 : LSA_MINB_F32)
+    k_arnoldi_flat(ArnoldiParams P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  using E = Engine<Op, Tc, Tc>;
+  typename E::Smem& S = *reinterpret_cast<typename E::Smem*>(smem_raw);
+  E e(P, S, reinterpret_cast<double*>(smem_raw + E::small_offset()));
+  if (!e.place()) return;
+  e.template run_hybrid<true>(reinterpret_cast<Tc*>(smem_raw + E::smem_bytes()));
+}
+
+template <class Op, class Tc>
+size_t flat_smem_bytes() {
+  return Engine<Op, Tc, Tc>::smem_bytes() + 2 * Engine<Op, Tc, Tc>::FCH * sizeof(Tc);
+}
+
 // One stencil pass y = A x with the same tile code (no barrier).
 template <class Op, class Tc, class B>
 __global__ void __launch_bounds__(NT) k_matvec(ArnoldiParams P, const B* x, B* y) {
@@ -1289,6 +1433,12 @@ cudaError_t launch_arnoldi_t(const ArnoldiParams& P, int G, cudaStream_t s) {
     if (P.naug > 0) k = k_arnoldi<Op, Tc, Tc, true>;
   }
   size_t sm = Engine<Op, Tc, Tc>::smem_bytes();
+  if constexpr (Op::KIND == LSA_OP_ADR3D) {
+    if (P.two_phase == 2 && P.naug == 0 && is_hybrid(P.variant)) {
+      k = k_arnoldi_flat<Op, Tc>;
+      sm = flat_smem_bytes<Op, Tc>();
+    }
+  }
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   return cudaLaunchCooperativeKernel((void*)k, dim3(G), dim3(NT), args, sm, s);
@@ -1324,6 +1474,24 @@ cudaError_t launch_matvec_op(const ArnoldiParams& P, int precision, const void* 
                              cudaStream_t s) {
   return precision == LSA_FP64 ? launch_matvec_t<Op, double>(P, x, y, G, s)
                                : launch_matvec_t<Op, float>(P, x, y, G, s);
+}
+
+// Resident CTAs per SM of the flat two-phase kernel (0 where it does not exist).
+template <class Op, class Tc>
+int flat_blocks_per_sm_t() {
+  int nb = 0;
+  if constexpr (Op::KIND == LSA_OP_ADR3D) {
+    auto k = k_arnoldi_flat<Op, Tc>;
+    size_t sm = flat_smem_bytes<Op, Tc>();
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, NT, sm);
+  }
+  return nb;
+}
+
+template <class Op>
+int flat_blocks_per_sm_op(int precision) {
+  return precision == LSA_FP64 ? flat_blocks_per_sm_t<Op, double>() : flat_blocks_per_sm_t<Op, float>();
 }
 
 template <class Op>

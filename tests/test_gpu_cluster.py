@@ -44,7 +44,7 @@ def run(cfg, variant, cluster, fn="phiv"):
 def test_cluster_kernel_matches_oracle_and_grid_kernel(cfg, variant):
     y_c, st_c = run(cfg, variant, True)
     y_g, st_g = run(cfg, variant, False)
-    assert st_c["arnoldi_kernel"] == 3 and st_g["arnoldi_kernel"] in (0, 4)
+    assert st_c["arnoldi_kernel"] == 3 and st_g["arnoldi_kernel"] in (0, 4, 5)
     ref, info = oracle_phiv(cfg)
     assert max(rel_errors(y_c, ref)) < FP64_TOL
     assert max(rel_errors(y_c, y_g)) < FP64_TOL

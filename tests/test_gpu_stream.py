@@ -49,7 +49,7 @@ def run(cfg, variant, stream):
 def test_stream_kernel_matches_oracle_and_plain_kernel(cfg, variant):
     y_s, st_s = run(cfg, variant, True)
     y_p, st_p = run(cfg, variant, False)
-    assert st_s["arnoldi_kernel"] == 2 and st_p["arnoldi_kernel"] in (0, 4)
+    assert st_s["arnoldi_kernel"] == 2 and st_p["arnoldi_kernel"] in (0, 4, 5)
     ref, info = oracle_phiv(cfg)
     assert max(rel_errors(y_s, ref)) < FP32_TOL
     assert max(rel_errors(y_p, ref)) < FP32_TOL

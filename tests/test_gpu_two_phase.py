@@ -178,3 +178,94 @@ def test_two_phase_adr256_full_size_matches_oracle():
     ref, info = oracle_phiv(cfg, "hcwy")
     assert max(rel_errors(y, ref)) < FP64_TOL
     assert st["m_eff"] == info["m_eff"] == cfg["m"]
+
+
+def _box3d(nx, ny, nz, **kw):
+    cfg = W.adr3d(nx, **kw)
+    cfg.update(ny=ny, nz=nz, name=f"adr3d_{nx}x{ny}x{nz}")
+    return cfg
+
+
+# ragged shares and chunks: N not a multiple of the 512-point chunk or of 32;
+# a two-plane z extent (both z neighbours are the other plane)
+FLAT_CASES = [W.adr3d(20, m=24, p=1), _box3d(33, 17, 9, m=20, p=2), _box3d(16, 8, 3, m=12, p=1),
+              _box3d(7, 5, 2, m=10, p=1), W.adr3d(64, m=40, p=1)]
+
+
+@pytest.mark.parametrize("cfg", FLAT_CASES, ids=[c["name"] for c in FLAT_CASES])
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_flat_two_phase_matches_tile_form_and_oracle(cfg, variant, precision):
+    """The flat two-phase step (3D, both passes over equal flat shares): w is
+    the tile passes' value, the inner products sum the points in other
+    groups, so basis and H agree with the tile form to rounding; the phi
+    product matches the oracle element by element, and the step takes one
+    barrier without a reduction besides its reduction."""
+    import paper_2410_14917_gb300 as lsa
+
+    op, v = _op(cfg)
+    m = min(cfg["m"], op.N)
+    out = {}
+    for two in (1, 2):
+        with _grid_kernel_env(two):
+            V, H, st = lsa.arnoldi(op, v, m, variant=variant, precision=precision)
+        out[two] = (V.cpu().numpy().astype(np.float64), H.cpu().numpy(), st)
+    (V1, H1, s1), (V2, H2, s2) = out[1], out[2]
+    assert s1["arnoldi_kernel"] == 4 and s2["arnoldi_kernel"] == 5
+    assert s2["status"] == 0 and s2["m_eff"] == s1["m_eff"] == m
+    tol = 1e-10 if precision == "fp64" else 1e-4
+    assert np.max(np.abs(H1 - H2)) <= tol * np.max(np.abs(H1))
+    assert np.max(np.abs(V1 - V2)) <= tol * np.max(np.abs(V1))
+    assert s2["grid_syncs"] == m + 1 + s2["norm_fallbacks"]
+    assert s2["grid_barriers"] == s2["grid_syncs"] + m
+    with _grid_kernel_env(2):
+        y, st = lsa.phiv(op, v, cfg["h"], cfg["p"], cfg["m"], variant=variant, precision=precision)
+    assert st["arnoldi_kernel"] == 5 and st["status"] == 0
+    ref, info = oracle_phiv(cfg, variant)
+    assert max(rel_errors(y, ref)) < (FP64_TOL if precision == "fp64" else FP32_TOL)
+    assert st["m_eff"] == info["m_eff"]
+
+
+def test_flat_two_phase_only_on_3d():
+    """LSA_TWO_PHASE=2 on a 2D operator runs the tile two-phase form."""
+    import paper_2410_14917_gb300 as lsa
+
+    cfg = W.advdiff2d(40, ny=23, m=16, p=1)
+    op, v = _op(cfg)
+    with _grid_kernel_env(2):
+        _, st = lsa.phiv(op, v, cfg["h"], cfg["p"], cfg["m"], variant="hcwy")
+    assert st["arnoldi_kernel"] == 4
+
+
+def test_flat_two_phase_adr256_fp32_matches_oracle():
+    """The flat form on the 3D ADR 256^3 workload with the float32 basis
+    (N = 16.7M, m = 40): the phi product against the oracle's H-CWY form,
+    element by element and normwise."""
+    import paper_2410_14917_gb300 as lsa
+
+    cfg = W.config(2)
+    op, v = _op(cfg)
+    with _grid_kernel_env(2):
+        y, st = lsa.phiv(op, v, cfg["h"], cfg["p"], cfg["m"], variant="hcwy", precision="fp32")
+    assert st["arnoldi_kernel"] == 5 and st["status"] == 0
+    ref, info = oracle_phiv(cfg, "hcwy")
+    assert max(rel_errors(y, ref)) < FP32_TOL
+    assert st["m_eff"] == info["m_eff"] == cfg["m"]
+
+
+def test_tune_step_3d_times_three_forms():
+    """On the 3D ADR operator in float64 the tuner also times the flat form;
+    later calls run the recorded form, and the float64 default (nothing
+    recorded) is the flat form."""
+    import paper_2410_14917_gb300 as lsa
+
+    cfg = W.adr3d(40, m=16, p=1)
+    op, v = _op(cfg)
+    os.environ.pop("LSA_TWO_PHASE", None)
+    with env(LSA_TMA=0, LSA_STREAM=0, LSA_CLUSTER=0):
+        _, st = lsa.phiv(op, v, cfg["h"], cfg["p"], cfg["m"], variant="hcwy")
+        assert st["arnoldi_kernel"] == 5
+        two, ms1, ms2 = lsa.tune_step(op, v, cfg["m"], variant="hcwy", precision="fp64", reps=1)
+        assert two in (0, 1, 2) and ms1 > 0 and ms2 > 0
+        _, st = lsa.phiv(op, v, cfg["h"], cfg["p"], cfg["m"], variant="hcwy")
+        assert st["arnoldi_kernel"] == (3 + two if two else 0)
