@@ -170,7 +170,8 @@ lsa_status lsa_arnoldi(const lsa_op* op, const double* v, int m, int variant, in
  * pass over tiles reads the projected vector back with its halo for the
  * stencil and the inner products: no repeated projection, one more barrier
  * per step; bitwise the basis and H of form 0.  Form 2, flat two-phase (the
- * 3D ADR operator): the second pass also runs over the equal flat shares,
+ * ADR 3D, advection-diffusion and Gray-Scott operators): the second pass also
+ * runs over the equal flat shares,
  * reading the stencil's neighbours through L2, with no tiles; the same
  * stencil values, inner products summed over other groups of points (equal
  * to forms 0 and 1 to rounding).
@@ -180,9 +181,9 @@ lsa_status lsa_arnoldi(const lsa_op* op, const double* v, int m, int variant, in
  * operator kind and grid, m, variant and precision use it (process-wide
  * table, thread-safe).  LSA_TWO_PHASE=0, 1 or 2 in the environment overrides
  * the table (2 runs form 1 where form 2 does not apply).  Without either:
- * form 2 for float64 3D grids, form 1 for float32-basis 3D grids and for
- * float64 2D grids of at least six 16 x 16 tiles per SM, form 0 otherwise
- * (the crossovers measured on GB300).
+ * form 2 for float64 3D grids and for 2D grids of at least six 16 x 16 tiles
+ * per SM, form 1 for float32-basis 3D grids, form 0 otherwise (the
+ * crossovers measured on GB300).
  *  v      dev, N doubles: start vector of the timing runs (not modified).
  *  work   dev workspace of lsa_workspace_bytes(op, m, 0, precision).
  *  reps   timed runs per form (>= 1; one untimed run precedes them).

@@ -214,7 +214,8 @@ def tune_step(op: Operator, v: torch.Tensor, m: int, variant="hcwy", precision="
               work=None, stream=None):
     """Times the step forms of the grid Arnoldi kernel's hybrid variants (0
     one-pass; 1 two-phase, its second pass over tiles; 2 flat two-phase, on
-    the 3D ADR operator) on (op, m, variant, precision) (lsa_tune_step) and
+    the ADR 3D, advection-diffusion and Gray-Scott operators) on (op, m,
+    variant, precision) (lsa_tune_step) and
     records the fastest for later calls with that shape.  Returns (form, ms of
     form 0, ms of the fastest two-phase form); (0, 0.0, 0.0) when the forms do
     not apply."""

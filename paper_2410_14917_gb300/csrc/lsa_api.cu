@@ -21,6 +21,8 @@ int blocks_per_sm_advdiff2d(int);
 int blocks_per_sm_grayscott2d(int);
 int blocks_per_sm_adr3d(int);
 int flat_blocks_per_sm_adr3d(int);
+int flat_blocks_per_sm_advdiff2d(int);
+int flat_blocks_per_sm_grayscott2d(int);
 bool tma_applicable_advdiff2d(const DevOp&, const Tiling&, int, int);
 bool tma_applicable_grayscott2d(const DevOp&, const Tiling&, int, int);
 bool tma_applicable_adr3d(const DevOp&, const Tiling&, int, int);
@@ -203,9 +205,10 @@ static bool use_cluster(const ArnoldiParams& P, int precision) {
 
 // Step form of the grid kernel's hybrid variants: 0 one pass; 1 two-phase
 // (project over flat shares; grid barrier; stencil and inner products over
-// tiles: no halo projection, one more barrier per step); 2 flat two-phase (3D
-// grids of one species: the second pass also over flat shares, the stencil's
-// neighbours read through L2, no tile chain; its own kernel).  Chosen per
+// tiles: no halo projection, one more barrier per step); 2 flat two-phase (the
+// ADR 3D, advection-diffusion and Gray-Scott operators: the second pass also
+// over flat shares, the stencil's neighbours read through L2, no tile chain;
+// its own kernel).  Chosen per
 // device, operator shape, m, variant and precision:
 // LSA_TWO_PHASE=0/1/2 in the environment forces it (2 runs form 1 where the
 // flat kernel does not exist); otherwise the form that
@@ -213,9 +216,10 @@ static bool use_cluster(const ArnoldiParams& P, int precision) {
 // GB300: a two-phase form for 3D grids (the z-halo planes make the repeated
 // projection large): the flat one in float64 (ADR 256^3: 93 against 119 ms),
 // the tile one for the float32 basis (where it is used at all: the streaming
-// kernel runs those grids first); two-phase for float64 2D grids with at
-// least six 16x16 tiles per SM, one-pass below that (the extra barrier costs
-// more than the halo).
+// kernel runs those grids first); the flat form for 2D grids with at least
+// six 16x16 tiles per SM (Gray-Scott 512^2: 9.33 against 9.60 ms in float64,
+// 3.50 against 4.30 in float32), one-pass below that (the extra barrier
+// costs more than the halo).
 struct StepKey {
   int dev, kind, nx, ny, nz, m, variant, precision;
   bool operator<(const StepKey& o) const {
@@ -255,19 +259,26 @@ static int two_phase_choice(const ArnoldiParams& P, int precision) {
     if (it != g_step_choice.end()) return it->second;
   }
   if (P.op.nz > 1) return precision == LSA_FP64 ? 2 : 1;
-  return (precision == LSA_FP64 && P.tl.ntiles >= 6 * sm_count()) ? 1 : 0;
+  return P.tl.ntiles >= 6 * sm_count() ? 2 : 0;
 }
 
-// The flat two-phase kernel exists for the 3D ADR operator, and its grid must
-// be resident: as many CTAs per SM as the grid kernel's layout assumes.
+// The flat two-phase kernel exists for the ADR 3D, advection-diffusion and
+// Gray-Scott operators, and its grid must be resident: as many CTAs per SM as
+// the grid kernel's layout assumes.
 static bool flat_fits(const ArnoldiParams& P, int precision) {
-  if (P.op.kind != LSA_OP_ADR3D) return false;
-  static int cache[2][16];
+  const int kind = P.op.kind;
+  if (kind != LSA_OP_ADR3D && kind != LSA_OP_ADVDIFF2D && kind != LSA_OP_GRAYSCOTT2D) return false;
+  static int cache[6][2][16];
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 16) dev = 0;
-  int& c = cache[precision][dev];
-  if (c == 0) c = flat_blocks_per_sm_adr3d(precision) >= arnoldi_blocks_per_sm(P.op, precision) ? 1 : -1;
+  int& c = cache[kind][precision][dev];
+  if (c == 0) {
+    const int nb = kind == LSA_OP_ADR3D ? flat_blocks_per_sm_adr3d(precision)
+                   : kind == LSA_OP_ADVDIFF2D ? flat_blocks_per_sm_advdiff2d(precision)
+                                              : flat_blocks_per_sm_grayscott2d(precision);
+    c = nb >= arnoldi_blocks_per_sm(P.op, precision) ? 1 : -1;
+  }
   return c > 0;
 }
 

@@ -15,6 +15,7 @@ cudaError_t launch_matvec_advdiff2d(const ArnoldiParams& P, int precision, const
   return launch_matvec_op<OpAdvDiff2D>(P, precision, x, y, G, s);
 }
 int blocks_per_sm_advdiff2d(int precision) { return blocks_per_sm_op<OpAdvDiff2D>(precision); }
+int flat_blocks_per_sm_advdiff2d(int precision) { return flat_blocks_per_sm_op<OpAdvDiff2D>(precision); }
 bool tma_applicable_advdiff2d(const DevOp& d, const Tiling& tl, int m, int precision) {
   return precision == LSA_FP32_BASIS ? tma_applicable_op<OpAdvDiff2D, float>(d, tl, m)
                                      : tma_applicable_op<OpAdvDiff2D, double>(d, tl, m);

@@ -13,6 +13,7 @@ cudaError_t launch_matvec_grayscott2d(const ArnoldiParams& P, int precision, con
   return launch_matvec_op<OpGrayScott2D>(P, precision, x, y, G, s);
 }
 int blocks_per_sm_grayscott2d(int precision) { return blocks_per_sm_op<OpGrayScott2D>(precision); }
+int flat_blocks_per_sm_grayscott2d(int precision) { return flat_blocks_per_sm_op<OpGrayScott2D>(precision); }
 bool tma_applicable_grayscott2d(const DevOp& d, const Tiling& tl, int m, int precision) {
   return precision == LSA_FP32_BASIS ? tma_applicable_op<OpGrayScott2D, float>(d, tl, m)
                                      : tma_applicable_op<OpGrayScott2D, double>(d, tl, m);

@@ -292,26 +292,30 @@ struct Engine {
     }
   }
 
-  // Second pass of the flat two-phase step (3D grids of one species): this
-  // CTA's equal flat share (the first pass's share) in chunks of FCH points.
-  // Each thread forms w = A x at FQ points with the seven neighbours of x read
-  // through L2 (x was stored by the first pass, before the grid barrier; the
-  // grid is periodic in every direction, as in the tile passes), stores w and
-  // adds the self terms; then the warps form the inner products with basis
+  // Second pass of the flat two-phase step: this CTA's equal flat share of
+  // the grid points (all species of a point together) in chunks of FCH
+  // points.  Each thread forms w = A x at FQ points with the neighbours of x
+  // read through L2 (x was stored by the first pass, before the grid barrier;
+  // the grid is periodic in every direction, as in the tile passes), stores w
+  // and adds the self terms; then the warps form the inner products with basis
   // columns (warp <-> columns, lane <-> points, as in dots_plane) from the
-  // chunk's x and w in shared memory (xs, ws: FCH values each).  No halo copy,
-  // no tile chain: every CTA has the same number of points.  w is bitwise the
-  // tile passes' value (same operator arithmetic); the inner products sum the
-  // points in other groups, so they agree with the tile passes to rounding.
+  // chunk's x and w in shared memory (xs, ws: NS*FCH values each).  No halo
+  // copy, no tile chain: every CTA has the same number of points.  w is
+  // bitwise the tile passes' value (the operator's own arithmetic on the
+  // loaded values, staged with a row pitch of 2 and species 5 apart); the
+  // inner products sum the points in other groups, so they agree with the
+  // tile passes to rounding.
   static constexpr int FQ = 2, FCH = FQ * NT;
+  static constexpr bool kFlatOp =
+      Op::KIND == LSA_OP_ADR3D || Op::KIND == LSA_OP_ADVDIFF2D || Op::KIND == LSA_OP_GRAYSCOTT2D;
   __device__ int run_pass_flat(const PassT<B>& ps, Tc* xs, Tc* ws) {
-    static_assert(NS == 1 && DIM == 3, "the flat pass is written for 3D grids of one species");
+    static_assert(kFlatOp, "the flat pass is written for the ADR 3D, advection-diffusion and Gray-Scott operators");
     const DevOp& d = P.op;
-    const long long N = d.N;
-    long long per = (N + gsize - 1) / gsize;
-    per = (per + 31) & ~31LL;                  // the shares of project_flat
+    const long long np = d.npts;               // grid points (N = NS * np)
+    long long per = (np + gsize - 1) / gsize;
+    per = (per + 31) & ~31LL;
     const long long e0 = (long long)grank * per;
-    const long long e1 = min(N, e0 + per);
+    const long long e1 = min(np, e0 + per);
     const B* xg = ps.srcB;
     const int nxy = d.nx * d.ny;
     const bool dx = ps.dmode & DOT_X, dw = ps.dmode & DOT_W;
@@ -320,88 +324,100 @@ struct Engine {
 #pragma unroll
       for (int u = 0; u < FQ; ++u) {
         const int pl = tid + u * NT;
-        Tc xv = (Tc)0, wv = (Tc)0;
+        Tc xv[NS], wv[NS];
+#pragma unroll
+        for (int sp = 0; sp < NS; ++sp) { xv[sp] = (Tc)0; wv[sp] = (Tc)0; }
         if (base + pl < e1) {
           // grid indices in 32 bits, as in the tile passes (N < 2^31)
           const int q = (int)base + pl;
           const int r = q / d.nx, ix = q - r * d.nx;
           const int iz = r / d.ny, iy = r - iz * d.ny;
-          // plane values in the layout Op::apply_f reads with a row pitch of 2:
-          // [south, west, centre, east, north]; below and above at index 2
-          Tc c5[5], zm[3], zp[3];
-          c5[2] = (Tc)__ldcg(xg + q);
-          c5[1] = (Tc)__ldcg(xg + (ix == 0 ? q + (d.nx - 1) : q - 1));
-          c5[3] = (Tc)__ldcg(xg + (ix == d.nx - 1 ? q - (d.nx - 1) : q + 1));
-          c5[0] = (Tc)__ldcg(xg + (iy == 0 ? q + (d.ny - 1) * d.nx : q - d.nx));
-          c5[4] = (Tc)__ldcg(xg + (iy == d.ny - 1 ? q - (d.ny - 1) * d.nx : q + d.nx));
-          zm[2] = (Tc)__ldcg(xg + (iz == 0 ? q + (d.nz - 1) * nxy : q - nxy));
-          zp[2] = (Tc)__ldcg(xg + (iz == d.nz - 1 ? q - (d.nz - 1) * nxy : q + nxy));
+          const int qw = ix == 0 ? q + (d.nx - 1) : q - 1;
+          const int qe = ix == d.nx - 1 ? q - (d.nx - 1) : q + 1;
+          const int qs = iy == 0 ? q + (d.ny - 1) * d.nx : q - d.nx;
+          const int qn = iy == d.ny - 1 ? q - (d.ny - 1) * d.nx : q + d.nx;
+          // per species: [south, west, centre, east, north]; below and above at index 2
+          Tc c5[5 * NS], zm[3], zp[3];
+#pragma unroll
+          for (int sp = 0; sp < NS; ++sp) {
+            const B* xsp = xg + (long long)sp * np;
+            c5[5 * sp + 0] = (Tc)__ldcg(xsp + qs);
+            c5[5 * sp + 1] = (Tc)__ldcg(xsp + qw);
+            c5[5 * sp + 2] = (Tc)__ldcg(xsp + q);
+            c5[5 * sp + 3] = (Tc)__ldcg(xsp + qe);
+            c5[5 * sp + 4] = (Tc)__ldcg(xsp + qn);
+          }
           zm[0] = zm[1] = zp[0] = zp[1] = (Tc)0;
-          Tc rr;
-          if constexpr (F64) rr = (Tc)__ldg(d.f0 + q);
-          else rr = (Tc)__ldg(d.g0 + q);
-          Tc out[1];
-          Op::template apply_f<Tc, 2>(cf, zm, c5, zp, 2, rr, (Tc)0, out);
-          xv = c5[2];
-          wv = out[0];
-          if constexpr (!F64) wv = (Tc)(B)wv;
-          ps.wout[q] = (B)wv;
-          if (ps.self & SELF_XX) self_add(0, xv, xv);
-          if (ps.self & SELF_XW) self_add(1, xv, wv);
-          if (ps.self & SELF_WW) self_add(2, wv, wv);
+          if constexpr (DIM == 3) {
+            zm[2] = (Tc)__ldcg(xg + (iz == 0 ? q + (d.nz - 1) * nxy : q - nxy));
+            zp[2] = (Tc)__ldcg(xg + (iz == d.nz - 1 ? q - (d.nz - 1) * nxy : q + nxy));
+          } else {
+            zm[2] = zp[2] = (Tc)0;
+          }
+          Tc out[NS];
+          Op::template apply<Tc, 2, 5>(d, cf, zm, c5, zp, 2, (long long)q, out);
+#pragma unroll
+          for (int sp = 0; sp < NS; ++sp) {
+            Tc w = out[sp];
+            if constexpr (!F64) w = (Tc)(B)w;
+            const Tc x = c5[5 * sp + 2];
+            ps.wout[(long long)sp * np + q] = (B)w;
+            if (ps.self & SELF_XX) self_add(0, x, x);
+            if (ps.self & SELF_XW) self_add(1, x, w);
+            if (ps.self & SELF_WW) self_add(2, w, w);
+            xv[sp] = x;
+            wv[sp] = w;
+          }
         }
-        xs[pl] = xv;
-        ws[pl] = wv;
+#pragma unroll
+        for (int sp = 0; sp < NS; ++sp) {
+          xs[sp * FCH + pl] = xv[sp];
+          ws[sp * FCH + pl] = wv[sp];
+        }
       }
       __syncthreads();
       if (ps.d1 > ps.d0) {
-        // lane l takes points l + 32k of the chunk, k < FCH/32, in groups of 8;
-        // CK columns' loads in flight together (two spill registers in the
-        // float32 kernel, so one)
+        // lane l takes points l + 32k of the chunk, k < FCH/32, in groups of
+        // 8, one species after the other
         constexpr int NPL = FCH / 32;
-        constexpr int CK = 1;
         const int nv = (int)min((long long)FCH, e1 - base);   // valid points of the chunk
+#pragma unroll 1
+        for (int sp = 0; sp < NS; ++sp) {
+          const Tc* xsp = xs + sp * FCH;
+          const Tc* wsp = ws + sp * FCH;
 #pragma unroll
-        for (int kk = 0; kk < KMAX; kk += CK) {
-          if (ps.d0 + warp + NW * kk >= ps.d1) break;
-          Tc v[CK][NPL];
+          for (int kk = 0; kk < KMAX; ++kk) {
+            const int c = ps.d0 + warp + NW * kk;
+            if (c >= ps.d1) break;
+            const B* col = Vc(c) + (long long)sp * np + base;
+            Tc v[NPL];
 #pragma unroll
-          for (int i = 0; i < CK; ++i) {
-            const int c = ps.d0 + warp + NW * (kk + i);
-            if (c < ps.d1) {
-              const B* col = Vc(c) + base;
-#pragma unroll
-              for (int k = 0; k < NPL; ++k) {
-                const int pl = lane + 32 * k;
-                v[i][k] = (Tc)__ldcg(col + (pl < nv ? pl : 0));   // beyond the share: x = w = 0 there
-              }
+            for (int k = 0; k < NPL; ++k) {
+              const int pl = lane + 32 * k;
+              v[k] = (Tc)__ldcg(col + (pl < nv ? pl : 0));   // beyond the share: x = w = 0 there
             }
-          }
-#pragma unroll
-          for (int i = 0; i < CK; ++i) {
-            if (ps.d0 + warp + NW * (kk + i) >= ps.d1) break;
 #pragma unroll
             for (int g = 0; g < NPL / 8; ++g) {
               if constexpr (F64) {
-                double a = ax[kk + i], b = aw[kk + i];
+                double a = ax[kk], b = aw[kk];
 #pragma unroll
                 for (int k = 8 * g; k < 8 * g + 8; ++k) {
                   const int pl = lane + 32 * k;
-                  if (dx) a = fma((double)v[i][k], (double)xs[pl], a);
-                  if (dw) b = fma((double)v[i][k], (double)ws[pl], b);
+                  if (dx) a = fma((double)v[k], (double)xsp[pl], a);
+                  if (dw) b = fma((double)v[k], (double)wsp[pl], b);
                 }
-                ax[kk + i] = a;
-                aw[kk + i] = b;
+                ax[kk] = a;
+                aw[kk] = b;
               } else {
                 float px = 0.f, pw = 0.f;
 #pragma unroll
                 for (int k = 8 * g; k < 8 * g + 8; ++k) {
                   const int pl = lane + 32 * k;
-                  px = fmaf((float)v[i][k], (float)xs[pl], px);
-                  pw = fmaf((float)v[i][k], (float)ws[pl], pw);
+                  px = fmaf((float)v[k], (float)xsp[pl], px);
+                  pw = fmaf((float)v[k], (float)wsp[pl], pw);
                 }
-                if (dx) kahan(axs[kk + i], axc[kk + i], px);
-                if (dw) kahan(aws[kk + i], awc[kk + i], pw);
+                if (dx) kahan(axs[kk], axc[kk], px);
+                if (dw) kahan(aws[kk], awc[kk], pw);
               }
             }
           }
@@ -1107,9 +1123,9 @@ struct Engine {
   // x_j = u_j / nrm_est_{j-1} (u_j the projected vector); the normalised
   // v_j = sigma_j x_j with sigma_j = 1/||x_j|| known after step j.  All the
   // rescalings of Alg. 4 are folded into the scalars a, coef and sigma.
-  // kFlat: the instantiation of k_arnoldi_flat (3D grids of one species),
-  // whose two-phase step runs run_pass_flat after the flat projection (fbuf:
-  // 2*FCH values of shared memory); the other kernels carry none of its code.
+  // kFlat: the instantiation of k_arnoldi_flat, whose two-phase step runs
+  // run_pass_flat after the flat projection (fbuf: 2*NS*FCH values of shared
+  // memory); the other kernels carry none of its code.
   template <bool kFlat = false>
   __device__ void run_hybrid(Tc* fbuf = nullptr) {
     B* V = reinterpret_cast<B*>(P.V);
@@ -1146,7 +1162,7 @@ struct Engine {
         ps.xout = nullptr;
       }
       int ns;
-      if constexpr (kFlat) ns = two ? run_pass_flat(ps, fbuf, fbuf + FCH) : run_pass(ps);
+      if constexpr (kFlat) ns = two ? run_pass_flat(ps, fbuf, fbuf + NS * FCH) : run_pass(ps);
       else ns = run_pass(ps);
       if (!reduce_step(gen, ns, j, [&] { hybrid_step(j); }, j - 1)) return;
       if (S.done) return;
@@ -1391,8 +1407,9 @@ __global__ void __launch_bounds__(NT, (sizeof(Tc) == 8) ? LSA_MINB_F64 : LSA_MIN
   else e.run_hybrid();
 }
 
-// The hybrid variants with the flat two-phase step (3D grids of one species):
-// a separate instantiation with 2*FCH values of extra shared memory.
+// The hybrid variants with the flat two-phase step (the ADR 3D,
+// advection-diffusion and Gray-Scott operators): a separate instantiation
+// with 2*NS*FCH values of extra shared memory.
 template <class Op, class Tc>
 __global__ void __launch_bounds__(NT, (sizeof(Tc) == 8) ? LSA_MINB_F64 : LSA_MINB_F32)
     k_arnoldi_flat(ArnoldiParams P) {
@@ -1406,7 +1423,7 @@ __global__ void __launch_bounds__(NT, (sizeof(Tc) == 8) ? LSA_MINB_F64 : LSA_MIN
 
 template <class Op, class Tc>
 size_t flat_smem_bytes() {
-  return Engine<Op, Tc, Tc>::smem_bytes() + 2 * Engine<Op, Tc, Tc>::FCH * sizeof(Tc);
+  return Engine<Op, Tc, Tc>::smem_bytes() + 2 * Op::NS * Engine<Op, Tc, Tc>::FCH * sizeof(Tc);
 }
 
 // One stencil pass y = A x with the same tile code (no barrier).
@@ -1433,7 +1450,7 @@ cudaError_t launch_arnoldi_t(const ArnoldiParams& P, int G, cudaStream_t s) {
     if (P.naug > 0) k = k_arnoldi<Op, Tc, Tc, true>;
   }
   size_t sm = Engine<Op, Tc, Tc>::smem_bytes();
-  if constexpr (Op::KIND == LSA_OP_ADR3D) {
+  if constexpr (Engine<Op, Tc, Tc>::kFlatOp) {
     if (P.two_phase == 2 && P.naug == 0 && is_hybrid(P.variant)) {
       k = k_arnoldi_flat<Op, Tc>;
       sm = flat_smem_bytes<Op, Tc>();
@@ -1480,7 +1497,7 @@ cudaError_t launch_matvec_op(const ArnoldiParams& P, int precision, const void* 
 template <class Op, class Tc>
 int flat_blocks_per_sm_t() {
   int nb = 0;
-  if constexpr (Op::KIND == LSA_OP_ADR3D) {
+  if constexpr (Engine<Op, Tc, Tc>::kFlatOp) {
     auto k = k_arnoldi_flat<Op, Tc>;
     size_t sm = flat_smem_bytes<Op, Tc>();
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

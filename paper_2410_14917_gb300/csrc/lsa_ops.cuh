@@ -26,7 +26,7 @@ struct Coef {
 // 2D periodic advection-diffusion: A v = c Lap5 v - u.grad v (central).
 struct OpAdvDiff2D {
   static constexpr int NS = 1, DIM = 2, KIND = LSA_OP_ADVDIFF2D, NF = 0;
-  template <class Tc, int RP = PW>
+  template <class Tc, int RP = PW, int SP = PS>
   __device__ __forceinline__ static void apply_f(const Coef<Tc>& c, const Tc* zm, const Tc* z0,
                                                  const Tc* zp, int o, Tc, Tc, Tc* out) {
     (void)zm; (void)zp;
@@ -38,11 +38,11 @@ struct OpAdvDiff2D {
     r = fma(c.cN, z0[o + RP], r);
     out[0] = r;
   }
-  template <class Tc>
+  template <class Tc, int RP = PW, int SP = PS>
   __device__ __forceinline__ static void apply(const DevOp&, const Coef<Tc>& c, const Tc* zm,
                                                const Tc* z0, const Tc* zp, int o, long long,
                                                Tc* out) {
-    apply_f<Tc>(c, zm, z0, zp, o, (Tc)0, (Tc)0, out);
+    apply_f<Tc, RP, SP>(c, zm, z0, zp, o, (Tc)0, (Tc)0, out);
   }
 };
 
@@ -51,7 +51,8 @@ struct OpAdvDiff2D {
 // float32 form.
 struct OpGrayScott2D {
   static constexpr int NS = 2, DIM = 2, KIND = LSA_OP_GRAYSCOTT2D, NF = 2;
-  template <class Tc, int RP = PW>
+  // RP: row pitch of the staged values; SP: offset of the second species
+  template <class Tc, int RP = PW, int SP = PS>
   __device__ __forceinline__ static void apply_f(const Coef<Tc>& c, const Tc* zm, const Tc* z0,
                                                  const Tc* zp, int o, Tc f0, Tc f1, Tc* out) {
     (void)zm; (void)zp;
@@ -59,21 +60,21 @@ struct OpGrayScott2D {
     if constexpr (sizeof(Tc) == 8) { a = f1 * f1; b = (Tc)2 * f0 * f1; }
     else { a = f0; b = f1; }
     const Tc* U = z0;
-    const Tc* Vv = z0 + PS;
+    const Tc* Vv = z0 + SP;
     Tc u = U[o], v = Vv[o];
     Tc lu = (U[o - 1] + U[o + 1]) + (U[o - RP] + U[o + RP]) - (Tc)4 * u;
     Tc lv = (Vv[o - 1] + Vv[o + 1]) + (Vv[o - RP] + Vv[o + RP]) - (Tc)4 * v;
     out[0] = c.du * lu - (a + c.F) * u - b * v;
     out[1] = c.dv * lv + (b - c.F - c.k) * v + a * u;
   }
-  template <class Tc>
+  template <class Tc, int RP = PW, int SP = PS>
   __device__ __forceinline__ static void apply(const DevOp& d, const Coef<Tc>& c, const Tc* zm,
                                                const Tc* z0, const Tc* zp, int o, long long gpt,
                                                Tc* out) {
     Tc f0, f1;
     if constexpr (sizeof(Tc) == 8) { f0 = __ldg(d.f0 + gpt); f1 = __ldg(d.f1 + gpt); }
     else { f0 = __ldg(d.g0 + gpt); f1 = __ldg(d.g1 + gpt); }
-    apply_f<Tc>(c, zm, z0, zp, o, f0, f1, out);
+    apply_f<Tc, RP, SP>(c, zm, z0, zp, o, f0, f1, out);
   }
 };
 
@@ -147,7 +148,7 @@ struct OpGrayScottFrechet2D {
 // 3D periodic advection-diffusion-reaction with first-order upwinding.
 struct OpADR3D {
   static constexpr int NS = 1, DIM = 3, KIND = LSA_OP_ADR3D, NF = 1;
-  template <class Tc, int RP = PW>
+  template <class Tc, int RP = PW, int SP = PS>
   __device__ __forceinline__ static void apply_f(const Coef<Tc>& c, const Tc* zm, const Tc* z0,
                                                  const Tc* zp, int o, Tc rr, Tc, Tc* out) {
     Tc x = z0[o];
@@ -160,14 +161,14 @@ struct OpADR3D {
     r = fma(c.cU, zp[o], r);
     out[0] = r;
   }
-  template <class Tc>
+  template <class Tc, int RP = PW, int SP = PS>
   __device__ __forceinline__ static void apply(const DevOp& d, const Coef<Tc>& c, const Tc* zm,
                                                const Tc* z0, const Tc* zp, int o, long long gpt,
                                                Tc* out) {
     Tc rr;
     if constexpr (sizeof(Tc) == 8) rr = __ldg(d.f0 + gpt);
     else rr = __ldg(d.g0 + gpt);
-    apply_f<Tc>(c, zm, z0, zp, o, rr, (Tc)0, out);
+    apply_f<Tc, RP, SP>(c, zm, z0, zp, o, rr, (Tc)0, out);
   }
 };
 
