@@ -5,8 +5,9 @@
 // the grid tile by tile: it projects a vector (x = a*src - sum_c coef_c V_c),
 // optionally applies the stencil (w = A x, needing the projection on a
 // one-point halo, recomputed redundantly by each tile -- or, in the two-phase
-// form of the hybrid step, projected once over flat shares and read back
-// after a grid barrier), and accumulates inner products of basis columns with
+// forms of the hybrid step, projected once over flat shares and read back
+// after a grid barrier, by the tiles or, in the flat form, over flat shares
+// of the points again), and accumulates inner products of basis columns with
 // x and/or w.  The per-CTA partial sums go to
 // global memory, and one grid barrier reduces them in two levels: the last CTA
 // of each group of RG CTAs sums its group, the last group sums the group rows
