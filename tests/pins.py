@@ -255,6 +255,53 @@ def pin_arnoldi_relation(variant):
     return np.linalg.norm(R) / (scipy.sparse.linalg.norm(A) * np.linalg.norm(V))
 
 
+def prescribed_columns(N=200, n=31, kappa=1e7, seed=5):
+    """X = U diag(1 .. 1/kappa) W^T (N x n, 2-norm condition number kappa) and
+    a "matvec" that returns X's next column at each call, ignoring its input:
+    driven by it, every Arnoldi variant becomes a Gram-Schmidt QR of X, where
+    the textbook bounds on the loss of orthogonality apply."""
+    rng = np.random.default_rng(seed)
+    U, _ = np.linalg.qr(rng.standard_normal((N, n)))
+    W_, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    X = U @ np.diag(np.logspace(0, -np.log10(kappa), n)) @ W_.T
+    calls = [0]
+
+    def next_column(_v):
+        calls[0] += 1
+        return X[:, calls[0]].copy()
+    return X, next_column, calls
+
+
+def orthogonality_loss(variant, kappa):
+    """||I - V^T V||_2 of the basis a variant computes from X (the QR reading
+    above) and the column count driven; the start vector is X's first column."""
+    X, f, calls = prescribed_columns(kappa=kappa)
+    m = X.shape[1] - 1
+    res = OA.arnoldi(f, X[:, 0], m, variant)
+    V = res["V"]
+    assert calls[0] == m and res["m_eff"] == m
+    return np.linalg.norm(np.eye(V.shape[1]) - V.T @ V, 2)
+
+
+def pin_orthogonality_laws(kappas=(1e4, 1e7)):
+    """The loss of orthogonality against its textbook laws, as a ratio that
+    is <= 1 when every law holds: modified Gram-Schmidt loses at most
+    c eps kappa(X) (Bjorck 1967), and the hybrid corrections, which the paper
+    says are as accurate as MGS, are held to the same law; classical
+    Gram-Schmidt applied twice keeps O(eps) whatever kappa(X) is ("twice is
+    enough": Giraud, Langou and Rozloznik 2005), held to 10 n eps here.
+    Classical Gram-Schmidt once, which a dropped or wrong correction turns the
+    hybrid step into, loses eps kappa^2 and fails the MGS law."""
+    eps = np.finfo(float).eps
+    n = 31
+    worst = 0.0
+    for kappa in kappas:
+        for var in ("mgs", "hcwy", "hncwy", "hgsmgs"):
+            worst = max(worst, orthogonality_loss(var, kappa) / (2.0 * eps * kappa))
+        worst = max(worst, orthogonality_loss("cgs2", kappa) / (10.0 * n * eps))
+    return worst
+
+
 # --- phi products -------------------------------------------------------------------
 
 def pin_krylov_vs_dense(variant="mgs"):

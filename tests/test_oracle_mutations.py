@@ -40,6 +40,32 @@ def test_gsmgs_transposed_splitting_is_caught(monkeypatch):
     assert pins.pin_gsmgs_two_sweeps() > 1e-3
 
 
+def test_hybrid_without_correction_is_caught(monkeypatch):
+    # T left at the identity: the hybrid step becomes classical Gram-Schmidt once
+    def no_correction(self, temp, j):
+        return temp[:j, 1].copy()
+    monkeypatch.setattr(OA.CWY, "form", no_correction)
+    assert pins.pin_orthogonality_laws() > 10.0
+
+
+def test_cgs2_single_pass_is_caught(monkeypatch):
+    def cgs_once(matvec, b, m):
+        b = np.asarray(b, dtype=np.float64)
+        V = np.zeros((b.size, m + 1))
+        H = np.zeros((m + 1, m))
+        beta = np.linalg.norm(b)
+        V[:, 0] = b / beta
+        for j in range(1, m + 1):
+            w = matvec(V[:, j - 1])
+            H[:j, j - 1] = V[:, :j].T @ w      # the second projection left out
+            w = w - V[:, :j] @ H[:j, j - 1]
+            H[j, j - 1] = np.linalg.norm(w)
+            V[:, j] = w / H[j, j - 1]
+        return dict(V=V, H=H, beta=beta, m_eff=m, syncs=[2] * m, fallbacks=0, breakdown=False)
+    monkeypatch.setitem(OA.VARIANTS, "cgs2", cgs_once)
+    assert pins.pin_orthogonality_laws() > 10.0
+
+
 def test_hybrid_missing_second_scaling_is_caught(monkeypatch):
     orig = OA.hybrid
 

@@ -61,6 +61,11 @@ def test_variants_equal_mgs():
     assert pins.pin_variants_equal_mgs() < 1e-11
 
 
+def test_orthogonality_follows_textbook_laws():
+    # MGS and the hybrid corrections within 2 eps kappa(X), CGS2 within 10 n eps
+    assert pins.pin_orthogonality_laws() <= 1.0
+
+
 @pytest.mark.parametrize("variant", VARIANTS)
 def test_arnoldi_relation(variant):
     assert pins.pin_arnoldi_relation(variant) < 1e-14
