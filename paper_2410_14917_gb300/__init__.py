@@ -215,10 +215,9 @@ def tune_step(op: Operator, v: torch.Tensor, m: int, variant="hcwy", precision="
     """Times the step forms of the grid Arnoldi kernel's hybrid variants (0
     one-pass; 1 two-phase, its second pass over tiles; 2 flat two-phase, on
     the ADR 3D, advection-diffusion and Gray-Scott operators) on (op, m,
-    variant, precision) (lsa_tune_step) and
-    records the fastest for later calls with that shape.  Returns (form, ms of
-    form 0, ms of the fastest two-phase form); (0, 0.0, 0.0) when the forms do
-    not apply."""
+    variant, precision) (lsa_tune_step) and records the fastest for later
+    calls with that shape.  Returns (form, ms of form 0, ms of the fastest
+    two-phase form); (0, 0.0, 0.0) when the forms do not apply."""
     if v.dtype != torch.float64 or not v.is_cuda or not v.is_contiguous() or v.numel() != op.N:
         raise ValueError("v must be a contiguous float64 CUDA tensor of N values")
     m = min(int(m), op.N)
